@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Throughput of y = sgn(gamma5 D_w(mu)) x by the nested Krylov method on GB300.
+
+Workload (one "step" = one whole batched apply: outer Krylov steps, inner levels,
+Roberts-Higham, recombination): 16^4 lattice, near-unit SU(3) links exp(i 0.3 H)
+(seed 0), mu = 0.2, m_w = -1.6, the 12 spin-colour point sources at site 0,
+stopping tolerance 1e-8, k <= 1000, l = 72, double-float vectors on the float pipes
+with float links. An apply counts when its a-posteriori estimate is <= 1e-8.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun (N > 1) every rank runs its own batch
+on its own GPU (independent replicas, no collective on the data path) and the time
+is the maximum over ranks.
+"""
+import os
+
+# the CPU oracle leg runs single-threaded BLAS (set before numpy is imported)
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import re  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sgn(γ5D_w)x applies/s at 16^4, μ=0.2, rel.err≤1e-8; stencil % of HBM peak"
+DIMS = (16, 16, 16, 16)
+MU, M_W, EPS = 0.2, -1.6, 0.3
+TOL, K_MAX, L_INNER = 1e-8, 1000, 72
+NRHS = 12
+PREC = "df64"
+CHECK_FIRST, CHECK_EVERY = 100, 25
+STENCIL_SOURCES = ["paper_0910_2918_gb300/csrc/ov_outer.cu", "paper_0910_2918_gb300/csrc/ov_types.cuh"]
+PROFILE = os.path.join(ROOT, "profiles", "stencil_twosided_df64_16x16x16x16_12rhs.md")
+
+
+def workload_desc():
+    return (f"{DIMS[0]}^4 lattice, near-unit links eps={EPS} (seed 0), mu={MU}, m_w={M_W}, "
+            f"{NRHS} spin-colour point sources at site 0, tol {TOL:g}, k<={K_MAX}, l={L_INNER}, "
+            f"checks at k={CHECK_FIRST}+{CHECK_EVERY}j, double-float vectors / float links")
+
+
+def make_inputs():
+    import ovinputs as oi
+
+    U = oi.gauge_field(DIMS, "near_unit", 0, eps=EPS)
+    X = oi.point_sources_12(DIMS, site=0)
+    return U, X
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in STENCIL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic():
+    """dram bytes per stencil launch from the committed ncu summary, if the kernel
+    source still has the hash the counters were taken with."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_hash():
+        return None
+    return float(t.group(1))
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = f"/tmp/ov_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except OSError:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(U, x, k_used, l_used, seconds_target=15.0):
+    """Time the oracle on a bounded sample of one right-hand side: outer two-sided
+    Lanczos steps until ~seconds_target, plus one inner level at the GPU's k; return
+    (applies/s extrapolated to k_used outer steps and k_used/CHECK_EVERY checks,
+    description)."""
+    from oracle import dirac, krylov
+
+    fA = lambda v: dirac.A_apply(U, v, DIMS, M_W, MU)
+    fAH = lambda v: dirac.AH_apply(U, v, DIMS, M_W, MU)
+    out = krylov.Outer(fA, fAH, x, False)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 3 or (time.perf_counter() - t0 < seconds_target * 0.8 and steps < k_used):
+        out.step()
+        steps += 1
+    t_step = (time.perf_counter() - t0) / steps
+    # one inner level at the GPU's k on a tridiagonal of that size whose
+    # coefficients repeat the sampled ones (the cost depends only on k and l)
+    reps = int(np.ceil(k_used / steps))
+    a = np.tile(np.asarray(out.alpha, dtype=complex), reps)[:k_used]
+    b = np.tile(np.asarray(out.beta[1:steps + 1], dtype=complex), reps)[:k_used + 1]
+    g = np.tile(np.asarray(out.gamma[1:steps + 1], dtype=complex), reps)[:k_used + 1]
+    Hbig = krylov.tridiag(a, np.concatenate([[0], b]), np.concatenate([[0], g]))
+    t1 = time.perf_counter()
+    krylov.nested_sign_e1(Hbig, min(l_used, k_used), False)
+    t_inner = time.perf_counter() - t1
+    k_inner = k_used
+    n_checks = max(1, (k_used - CHECK_FIRST) // CHECK_EVERY + 1)
+    t_apply = k_used * t_step + n_checks * t_inner
+    desc = (f"oracle (numpy FP64) on 1 RHS: {steps} two-sided Lanczos steps timed "
+            f"({t_step:.3f} s/step) and one inner level (l={min(l_used, k_inner)}) at k={k_inner}; "
+            f"extrapolated to k={k_used} steps + {n_checks} checks")
+    return 1.0 / t_apply, desc, steps * t_step + (time.perf_counter() - t1)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_0910_2918_gb300 as ov
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    U, X = make_inputs()
+    n = X.shape[1]
+    stream = torch.cuda.Stream()
+    opts = ov.make_opts(check_interval=CHECK_EVERY, first_check=CHECK_FIRST, timing=1)
+    op = ov.Overlap(DIMS, U, M_W, MU, PREC, opts=opts, stream=stream.cuda_stream)
+    xd = torch.from_numpy(X).cuda()
+    yd = torch.zeros_like(xd)
+    xh = torch.from_numpy(X).pin_memory()
+    yh = torch.zeros_like(xh).pin_memory()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        rc, info = op.sign_apply(xd, yd, TOL, K_MAX, L_INNER)
+    torch.cuda.synchronize()
+    # timed region: device-resident inputs
+    op.reset_stats()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    good = 0
+    with Clocks(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            rc, info = op.sign_apply(xd, yd, TOL, K_MAX, L_INNER)
+            good += sum(1 for i in info if i["status"] == 0 and i["err_est"] <= TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    st = op.stats()
+    # end to end: host buffers, copies inside the call
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    good_e2e = 0
+    for _ in range(args.steps):
+        rc, info_e = op.sign_apply(xh.numpy(), yh.numpy(), TOL, K_MAX, L_INNER)
+        good_e2e += sum(1 for i in info_e if i["status"] == 0 and i["err_est"] <= TOL)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    barrier()
+    tmax = torch.tensor([ms, t_e2e * 1e3], dtype=torch.float64, device="cuda")
+    gsum = torch.tensor([good, good_e2e], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(gsum, op=dist.ReduceOp.SUM)
+    ms_max, e2e_ms = float(tmax[0]), float(tmax[1])
+    good_all, good_e2e_all = float(gsum[0]), float(gsum[1])
+    # accuracy against the double-precision path (outside the timed region, rank 0)
+    err_fp64 = None
+    if rank == 0 and not args.no_validate:
+        with ov.Overlap(DIMS, U, M_W, MU, "fp64", opts=ov.make_opts(check_interval=CHECK_EVERY,
+                                                                    first_check=CHECK_FIRST)) as ref:
+            sel = [0, 7]
+            yr = torch.zeros((len(sel), n), dtype=torch.complex128, device="cuda")
+            ref.sign_apply(xd[sel].contiguous(), yr, 1e-10, K_MAX, 100)
+            err_fp64 = max(float(torch.linalg.norm(yd[s] - yr[i]) / torch.linalg.norm(yr[i]))
+                           for i, s in enumerate(sel))
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        op.close()
+        return None
+    k_used = max(i["k"] for i in info)
+    l_used = max(i["l"] for i in info)
+    pk = peaks() or {}
+    hbm = pk.get("hbm_gbs")
+    peak_src = "of measured" if hbm else "of fallback"
+    hbm = hbm or 6800.0
+    # dominant kernel: the fused two-sided stencil step; algorithmic bytes per launch
+    V = int(np.prod(DIMS))
+    bytes_per_site = NRHS * 8 * 12 * 16 + 4 * 9 * 8  # 8 spinor passes of 16-byte complex, float links once
+    alg_bytes = V * bytes_per_site
+    n_st = st["stencil_launches"]
+    st_ms = st["stencil_ms"] / max(n_st, 1)
+    achieved = alg_bytes / (st_ms * 1e-3) / 1e9
+    traffic = profile_traffic()
+    value = world * NRHS * args.steps / (ms_max * 1e-3)
+    good_frac = good_all / (world * NRHS * args.steps)
+    cpu = None
+    if not args.no_cpu:
+        v, desc, spent = oracle_sample(U, X[0], k_used, l_used, args.cpu_seconds)
+        cpu = {"value": v, "unit": "applies/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": round(spent, 1)}
+    line = {
+        "metric": METRIC,
+        "value": value * good_frac,
+        "unit": "applies/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "df64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(), "global_batch": NRHS * world, "parallelism": f"replicas{world}",
+                   "l2": "working set per step >> L2 (12 x k x 12.6 MB stored basis)", "k_used": k_used,
+                   "l_used": l_used, "applies_within_tol": good_frac, "rel_err_vs_fp64_path": err_fp64},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "kernel": "k_step<PrecDF64, two-sided> (fused A, A^dag stencil + recurrence)",
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": st_ms, "peak_source": peak_src},
+        "phase_ms_per_step": {"stencil": st["stencil_ms"] / args.steps, "update": st["update_ms"] / args.steps,
+                              "inner": st["inner_ms"] / args.steps, "recombine": st["recombine_ms"] / args.steps},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * NRHS * args.steps / (e2e_ms * 1e-3) * (good_e2e_all / (world * NRHS * args.steps)),
+                "unit": "applies/s", "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(X.nbytes)},
+        "gpu_launches": int(st["launches"]),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    op.close()
+    return line
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, on the same workload and metric."""
+    if rank != 0:
+        return None
+    U, X = make_inputs()
+    k_assumed, l_used = 300, L_INNER
+    vals = []
+    desc = None
+    for i in range(args.warmup + args.steps):
+        v, desc, _ = oracle_sample(U, X[i % NRHS], k_assumed, l_used, seconds_target=args.cpu_seconds / 3)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "applies/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 / value,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(), "k_assumed": k_assumed},
+        "cpu_baseline": {"value": value, "unit": "applies/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-validate", action="store_true", help="skip the FP64-path accuracy check")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * libov -- y = sgn(gamma5 D_w(mu)) x by the nested Krylov subspace method, on one GB300.
+ *
+ * The operation is the one the overlap operator needs (Bloch & Heybrock, "A nested
+ * Krylov subspace method for the overlap operator", Lattice 2009):
+ *
+ *   D_ov(mu) = 1 + gamma5 sgn(gamma5 D_w(mu))                            (Sec. 1, Eq. (Dov))
+ *   sgn(A) x ~ ||x|| V_k sgn(H_k) e_1                                    (Sec. 2, Eq. (approximation))
+ *            ~ ||x|| V_k V_l sgn(H_l) e_1, inner space K_l(H_k + H_k^-1, e_1)
+ *                                                                        (Sec. 3, Eqs. (nested), (precond))
+ *   sgn(H) by S_{n+1} = (S_n + S_n^-1)/2, S_0 = H                        (Sec. 2, Eq. (Roberts))
+ *
+ * The outer basis comes from Lanczos at mu = 0 and two-sided (biorthogonal) Lanczos at
+ * mu != 0 (Sec. 2); each outer step is one stencil application of A = gamma5 D_w(mu)
+ * (and of A^dag = gamma5 D_w(-mu)) fused with the recurrence.
+ *
+ * Wilson-Dirac operator (the paper names it and its mass range -2 < m_w < 0, Sec. 1, but
+ * does not print it; this library uses the standard form):
+ *   (D_w psi)(x) = (m_w + 4) psi(x) - 1/2 sum_nu [ (1 - gamma_nu) e^{+mu d_{nu t}} U_nu(x) psi(x+nu)
+ *                                               + (1 + gamma_nu) e^{-mu d_{nu t}} U_nu(x-nu)^dag psi(x-nu) ]
+ * DeGrand-Rossi gamma basis (gamma5 = diag(1,1,-1,-1)), periodic in x, y, z and
+ * antiperiodic in t (optional).
+ *
+ * Layouts (canonical, at this boundary):
+ *   site   = x + Lx*(y + Ly*(z + Lz*t))
+ *   links  : complex double, interleaved (re, im), index ((site*4 + nu)*3 + a)*3 + b
+ *            for (U_nu(site))_{ab}; nu = 0..3 is x, y, z, t.
+ *   spinor : complex double, interleaved, index 12*site + 3*spin + colour (n = 12 V).
+ *   batches of spinors are contiguous: RHS r starts at r*n complex entries.
+ *
+ * Memory: every pointer argument is "host" or "device" as stated by the `mem` argument
+ * (OV_MEM_HOST / OV_MEM_DEVICE). Host buffers are copied synchronously inside the call;
+ * device buffers must stay valid until the call returns. The caller owns x, y and the
+ * links; the handle owns everything it allocates (converted links, Krylov bases,
+ * coefficients, inner-level scratch) and frees it in ov_destroy. All device work runs
+ * on the stream given to ov_create (NULL = legacy default stream); every entry point
+ * returns after that stream has finished the call's work.
+ *
+ * Errors: functions return OV_OK (0), a positive warning (OV_NOT_CONVERGED: y holds the
+ * best estimate and info->err_est is set) or a negative error; ov_strerror() names it.
+ * There is no CPU fallback: without a usable CUDA device every call fails with
+ * OV_ERR_CUDA.
+ */
+#ifndef OV_H
+#define OV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define OV_OK 0
+#define OV_NOT_CONVERGED 1      /* warning: tolerance not reached at k_max, or inner level too small */
+#define OV_ERR_ARG (-1)         /* bad argument: m_w outside (-2,0), dims, NULL pointer, l < 1, ... */
+#define OV_ERR_NOMEM (-2)       /* device allocation failed */
+#define OV_ERR_CUDA (-3)        /* a CUDA call failed (no device, launch error, ...) */
+#define OV_ERR_BREAKDOWN (-5)   /* serious breakdown of two-sided Lanczos (|w~^dag v~| ~ 0) */
+#define OV_ERR_RH_NOCONV (-6)   /* Roberts-Higham did not converge (singular inner matrix) */
+#define OV_ERR_TOO_LARGE (-7)   /* a size exceeds a documented device limit (e.g. l > 120) */
+
+/* ---- arithmetic of the outer (vector) level ---- */
+#define OV_PREC_FP64 0  /* double vectors and links, double arithmetic */
+#define OV_PREC_FP32 1  /* float vectors and links, float stencil; dot products, norms and all
+                           Krylov coefficients accumulated and kept in double */
+#define OV_PREC_DF64 2  /* float links (rounded once), vectors as unevaluated float pairs
+                           (hi + lo, ~48-bit significand) with error-free float arithmetic
+                           (Dekker 1971; Knuth TAOCP vol. 2 TwoSum); coefficients in double */
+
+#define OV_MEM_HOST 0
+#define OV_MEM_DEVICE 1
+
+/* ---- recombination mode ---- */
+#define OV_RECOMB_STORED 0   /* keep V_k in device memory and form ||x|| V_k c */
+#define OV_RECOMB_TWO_PASS 1 /* keep only the coefficients; regenerate v_j in a second pass */
+#define OV_RECOMB_AUTO 2     /* stored if V_k fits in free device memory, else two-pass */
+
+/* Lattice and precision description. */
+typedef struct {
+  int dims[4];        /* Lx, Ly, Lz, Lt; each >= 2 */
+  int precision;      /* OV_PREC_* */
+  int t_antiperiodic; /* 1: antiperiodic in t (default), 0: periodic */
+} ov_geom;
+
+/* Options; ov_default_opts() fills the defaults in brackets. */
+typedef struct {
+  int check_interval;   /* outer steps between stopping checks [10] */
+  int first_check;      /* first outer step at which the stopping check runs [check_interval] */
+  int recombination;    /* OV_RECOMB_* [OV_RECOMB_AUTO] */
+  double rh_tol;        /* Roberts-Higham stop: ||S_{n+1}-S_n||_F <= rh_tol ||S_{n+1}||_F [1e-10] */
+  int rh_maxit;         /* Roberts-Higham iteration cap [100] */
+  double breakdown_tol; /* relative breakdown threshold of the outer recurrences [1e-14] */
+  int inner_dl;         /* step of the inner estimate: c(l) vs c(l - inner_dl) [4] */
+  int k_fixed;          /* > 0: run exactly k_fixed outer steps, evaluate once, no stopping rule [0] */
+  int timing;           /* 1: record CUDA events around every stencil / update / inner / recombination
+                           launch on the handle's stream and accumulate their durations (ov_get_stats) [0] */
+} ov_opts;
+
+/* Launch counts and (with opts.timing) device time per kernel class, accumulated over
+ * calls since the last ov_reset_stats. Times are CUDA-event durations on the handle's
+ * stream, in milliseconds. */
+typedef struct {
+  long long launches;          /* every kernel libov launched */
+  long long stencil_launches;  /* fused stencil steps (outer level, both passes) */
+  long long update_launches;   /* vector updates */
+  long long inner_launches;    /* inner level (inner Krylov, Roberts-Higham, combine) */
+  long long other_launches;    /* pack, recombination, conversions */
+  double stencil_ms, update_ms, inner_ms, recombine_ms, total_ms;
+  long long outer_steps;       /* outer Krylov steps run (first pass) */
+  long long regen_steps;       /* steps of the second (regeneration) pass */
+  long long checks;            /* stopping checks (inner evaluations) */
+} ov_stats;
+
+/* Per-RHS result information. */
+typedef struct {
+  int k;          /* outer Krylov dimension used */
+  int l;          /* inner Krylov dimension used (<= l requested, <= k) */
+  int rh_iters;   /* Roberts-Higham iterations of the final evaluation */
+  int status;     /* OV_* status of this right-hand side */
+  double err_est; /* a-posteriori estimate max(outer, inner) (NaN with k_fixed) */
+  double err_inner; /* inner part of the estimate */
+} ov_info;
+
+typedef struct ov_handle ov_handle;
+
+void ov_default_opts(ov_opts* opts);
+const char* ov_strerror(int code);
+
+/* Create a handle for one gauge field: validates -2 < m_w < 0 (Sec. 1), copies the links
+ * (canonical layout, `links_mem` says host or device) into handle-owned device memory in
+ * the kernel layout (t-boundary sign folded in; rounded to float for FP32/DF64), and
+ * records mu. stream: a cudaStream_t or NULL. opts may be NULL (defaults). */
+int ov_create(ov_handle** h, const ov_geom* geom, const void* links, int links_mem,
+              double m_w, double mu, const ov_opts* opts, void* stream);
+void ov_destroy(ov_handle* h);
+
+/* Change the options of an existing handle (same meaning as in ov_create). */
+int ov_set_opts(ov_handle* h, const ov_opts* opts);
+
+/* Read / clear the handle's launch and timing statistics. */
+int ov_get_stats(const ov_handle* h, ov_stats* stats);
+int ov_reset_stats(ov_handle* h);
+
+/* y_r = sgn(gamma5 D_w(mu)) x_r for nrhs right-hand sides sharing the gauge field
+ * (Sec. 3, Eq. (nested)). x, y: nrhs * 12V complex doubles (canonical layout; `mem`
+ * says where). tol: stopping tolerance of the a-posteriori estimate; k_max: outer cap;
+ * l: inner dimension (1 <= l <= 120; l_eff = min(l, k)). info: array of nrhs entries
+ * (may be NULL). Returns the worst status over the right-hand sides. */
+int ov_sign_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol,
+                  int k_max, int l, ov_info* info);
+
+/* y_r = D_ov(mu) x_r = x_r + gamma5 sgn(gamma5 D_w(mu)) x_r (Sec. 1, Eq. (Dov)). */
+int ov_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max,
+             int l, ov_info* info);
+
+/* y_r = A x_r with A = gamma5 D_w(mu) (dagger = 0) or A^dag = gamma5 D_w(-mu)
+ * (dagger = 1): the stencil alone, in the handle's arithmetic (Sec. 1). */
+int ov_wilson_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, int dagger);
+
+/* Inner level alone (Sec. 3, Eqs. (nested), (precond)), batched over `count` Ritz
+ * matrices given by their tridiagonal coefficients in HOST memory:
+ *   alpha[i*ld + j], j < k[i]           diagonal H_{j,j}
+ *   beta [i*ld + j], 1 <= j < k[i]      subdiagonal H_{j,j-1}
+ *   gamma[i*ld + j], 1 <= j < k[i]      superdiagonal H_{j-1,j}
+ * (complex doubles, interleaved; hermitian = 1 means real symmetric H, imaginary parts
+ * ignored). For each matrix: c = Q_l sgn(T_l) e_1 ~ sgn(H) e_1 with l_eff = min(l, k[i]),
+ * written to c[i*ld + j] (complex double, host), and the inner estimate ||c - c'||/||c||
+ * (c' from l_eff - opts.inner_dl inner steps) to est_inner[i] (may be NULL); the RH
+ * iteration count to rh_iters[i] (may be NULL). k[i] <= ld <= 1024, l <= 120. */
+int ov_inner_sign(ov_handle* h, int count, int ld, const int* k, const void* alpha,
+                  const void* beta, const void* gamma, int hermitian, int l, void* c,
+                  double* est_inner, int* rh_iters);
+
+/* Roberts-Higham alone (Sec. 2, Eq. (Roberts)): S = sgn(T) for `count` dense m x m
+ * matrices (row-major complex doubles, HOST memory, m <= 120), written to S (host).
+ * Returns OV_ERR_RH_NOCONV if any matrix did not converge within opts.rh_maxit. */
+int ov_rh_sign(ov_handle* h, int count, int m, const void* T, void* S, int* iters);
+
+/* Library/device description: writes "libov <version> sm_<cc> <device name>". */
+int ov_version(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OV_H */

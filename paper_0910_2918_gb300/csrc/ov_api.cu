@@ -1,0 +1,814 @@
+// C-ABI entry points and host orchestration of the nested Krylov sign function.
+//
+// One call of ov_sign_apply runs, for a batch of right-hand sides sharing the gauge
+// field and in lockstep:
+//   pack x (norms -> v_1 = x/||x||)                        Sec. 2, Eq. (approximation)
+//   for j = 1..: fused stencil step + vector update        Sec. 2 (Lanczos / two-sided Lanczos)
+//     every check_interval steps: inner level on H_k       Sec. 3, Eqs. (nested), (precond)
+//       (Roberts-Higham on the inner l x l matrix)         Sec. 2, Eq. (Roberts)
+//       and the stopping estimates
+//   recombination y = ||x|| V_k c from the stored basis, or by regenerating v_j from
+//   the stored coefficients in a second pass (double pass, Sec. 4).
+// The only device->host traffic inside the loop is the per-check status readback.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ov_internal.h"
+
+using namespace ov;
+
+namespace {
+
+constexpr int kChunk = 64;  // outer basis slots per allocation chunk
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+cudaError_t grow(Buf& b, size_t bytes) {
+  if (b.bytes >= bytes) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return e;
+  }
+  b.bytes = bytes;
+  return cudaSuccess;
+}
+void release(Buf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+}  // namespace
+
+struct ov_handle {
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  Geometry g{};
+  int prec = OV_PREC_FP64;
+  int antiperiodic = 1;
+  double m_w = -1.5, mu = 0.0;
+  ov_opts o{};
+  Buf links;
+  // outer level
+  Buf xcanon, ycanon;             // canonical device copies for host buffers
+  Buf tv, tw, p, r, vring, wring;  // [nrhs][12V] vectors (rings hold 2 slots)
+  Buf yacc;                       // two-pass accumulator
+  std::vector<Buf> chunks;        // stored basis: chunk c holds slots c*kChunk.. [slot][rhs][12V]
+  int chunk_rhs = 0;              // nrhs the chunks were sized for
+  Buf coef_alp, coef_bet, coef_gam, coef_nv, coef_nw, coef_status, coef_kbreak;
+  Buf partials, counters, scale;
+  int cap_rhs = 0, cap_ld = 0;
+  // inner level
+  Buf iQ, iT, ileff, iS, is, irh_its, irh_ok, iperm, ifail;
+  Buf ck, cl, ckprev, cc_cur, cc_prev, cc_fin, cacc_cur, cacc_fin, c_est_in, c_est_out, c_rhst, c_rhit;
+  Buf vptr;  // device array of basis slot pointers for recombination
+  int inner_cap = 0, inner_ld = 0;
+  ov_stats stats{};
+  // event pairs recorded around timed launches: (class, start, stop)
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_class;
+  size_t ev_used = 0;
+};
+
+enum { kClsStencil = 0, kClsUpdate = 1, kClsInner = 2, kClsRecomb = 3, kClsTotal = 4 };
+
+// record the start event of a timed launch group (no-op unless opts.timing)
+static int tstart(ov_handle* h, int cls) {
+  if (!h->o.timing) return -1;
+  if (h->ev_used + 2 > h->ev_pool.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      h->ev_pool.push_back(e);
+    }
+    h->ev_class.resize(h->ev_pool.size() / 2);
+  }
+  const int slot = (int)(h->ev_used / 2);
+  h->ev_class[slot] = cls;
+  cudaEventRecord(h->ev_pool[h->ev_used], h->st);
+  h->ev_used += 2;
+  return slot;
+}
+static void tstop(ov_handle* h, int slot) {
+  if (slot < 0) return;
+  cudaEventRecord(h->ev_pool[2 * slot + 1], h->st);
+}
+// after the stream has drained: add the recorded durations to the statistics
+static void tcollect(ov_handle* h) {
+  for (size_t s = 0; s < h->ev_used / 2; ++s) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[2 * s], h->ev_pool[2 * s + 1]) != cudaSuccess) continue;
+    switch (h->ev_class[s]) {
+      case kClsStencil: h->stats.stencil_ms += ms; break;
+      case kClsUpdate: h->stats.update_ms += ms; break;
+      case kClsInner: h->stats.inner_ms += ms; break;
+      case kClsRecomb: h->stats.recombine_ms += ms; break;
+      default: h->stats.total_ms += ms; break;
+    }
+  }
+  h->ev_used = 0;
+}
+
+extern "C" int ov_get_stats(const ov_handle* h, ov_stats* s) {
+  if (!h || !s) return OV_ERR_ARG;
+  *s = h->stats;
+  return OV_OK;
+}
+
+extern "C" int ov_reset_stats(ov_handle* h) {
+  if (!h) return OV_ERR_ARG;
+  h->stats = ov_stats{};
+  return OV_OK;
+}
+
+#define CK(call)                                       \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) {                           \
+      fprintf(stderr, "libov: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? OV_ERR_NOMEM : OV_ERR_CUDA; \
+    }                                                  \
+  } while (0)
+
+static size_t vec_bytes(const ov_handle* h) { return vec_elem_bytes(h->prec) * 12 * (size_t)h->g.V; }
+
+extern "C" void ov_default_opts(ov_opts* o) {
+  if (!o) return;
+  o->check_interval = 10;
+  o->first_check = 0;
+  o->recombination = OV_RECOMB_AUTO;
+  o->rh_tol = 1e-10;
+  o->rh_maxit = 100;
+  o->breakdown_tol = 1e-14;
+  o->inner_dl = 4;
+  o->k_fixed = 0;
+  o->timing = 0;
+}
+
+extern "C" const char* ov_strerror(int code) {
+  switch (code) {
+    case OV_OK: return "ok";
+    case OV_NOT_CONVERGED: return "not converged (tolerance not reached at k_max or inner dimension too small)";
+    case OV_ERR_ARG: return "invalid argument";
+    case OV_ERR_NOMEM: return "device allocation failed";
+    case OV_ERR_CUDA: return "CUDA error";
+    case OV_ERR_BREAKDOWN: return "serious breakdown of the two-sided Lanczos recurrence";
+    case OV_ERR_RH_NOCONV: return "Roberts-Higham iteration did not converge";
+    case OV_ERR_TOO_LARGE: return "size exceeds a device limit";
+    default: return "unknown status";
+  }
+}
+
+static int check_opts(const ov_opts& o) {
+  if (o.check_interval < 1 || o.rh_maxit < 1 || !(o.rh_tol > 0) || o.inner_dl < 1 || o.k_fixed < 0 ||
+      o.first_check < 0 || o.recombination < 0 || o.recombination > 2 || !(o.breakdown_tol >= 0))
+    return OV_ERR_ARG;
+  return OV_OK;
+}
+
+extern "C" int ov_set_opts(ov_handle* h, const ov_opts* opts) {
+  if (!h || !opts) return OV_ERR_ARG;
+  if (check_opts(*opts) != OV_OK) return OV_ERR_ARG;
+  h->o = *opts;
+  return OV_OK;
+}
+
+// canonical links [V][4][3][3] -> [4][9][V], t-boundary sign folded into U_t(t = Lt-1)
+template <class T>
+__global__ void k_links(Geometry g, int anti, const double2* __restrict__ in, T* out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int t = s / (g.Lx * g.Ly * g.Lz);
+  for (int nu = 0; nu < 4; ++nu) {
+    const double sg = (nu == 3 && anti && t == g.Lt - 1) ? -1.0 : 1.0;
+    for (int e = 0; e < 9; ++e) {
+      const double2 z = in[((size_t)s * 4 + nu) * 9 + e];
+      T o;
+      o.x = sg * z.x;
+      o.y = sg * z.y;
+      out[(size_t)(nu * 9 + e) * g.V + s] = o;
+    }
+  }
+}
+
+extern "C" int ov_create(ov_handle** hp, const ov_geom* geom, const void* links, int links_mem, double m_w,
+                         double mu, const ov_opts* opts, void* stream) {
+  if (!hp || !geom || !links) return OV_ERR_ARG;
+  *hp = nullptr;
+  if (!(m_w > -2.0 && m_w < 0.0) || !isfinite(mu)) return OV_ERR_ARG;  // -2 < m_w < 0 (Sec. 1)
+  for (int d = 0; d < 4; ++d)
+    if (geom->dims[d] < 2) return OV_ERR_ARG;
+  if (geom->precision < 0 || geom->precision > 2) return OV_ERR_ARG;
+  if (links_mem != OV_MEM_HOST && links_mem != OV_MEM_DEVICE) return OV_ERR_ARG;
+  const long long V = (long long)geom->dims[0] * geom->dims[1] * geom->dims[2] * geom->dims[3];
+  if (V > (1LL << 30) / 12) return OV_ERR_TOO_LARGE;
+  ov_opts o;
+  ov_default_opts(&o);
+  if (opts) {
+    if (check_opts(*opts) != OV_OK) return OV_ERR_ARG;
+    o = *opts;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return OV_ERR_CUDA;
+  ov_handle* h = new ov_handle();
+  CK(cudaGetDevice(&h->dev));
+  h->st = (cudaStream_t)stream;
+  h->g = Geometry{(int)V, geom->dims[0], geom->dims[1], geom->dims[2], geom->dims[3]};
+  h->prec = geom->precision;
+  h->antiperiodic = geom->t_antiperiodic ? 1 : 0;
+  h->m_w = m_w;
+  h->mu = mu;
+  h->o = o;
+  const size_t canon = sizeof(double2) * 36 * (size_t)V;
+  const double2* src = (const double2*)links;
+  Buf tmp;
+  auto fail = [&](int code) {
+    release(tmp);
+    ov_destroy(h);
+    return code;
+  };
+  if (links_mem == OV_MEM_HOST) {
+    if (grow(tmp, canon) != cudaSuccess) return fail(OV_ERR_NOMEM);
+    if (cudaMemcpyAsync(tmp.p, links, canon, cudaMemcpyHostToDevice, h->st) != cudaSuccess) return fail(OV_ERR_CUDA);
+    src = (const double2*)tmp.p;
+  }
+  const size_t lb = (h->prec == OV_PREC_FP64 ? sizeof(double2) : sizeof(float2)) * 36 * (size_t)V;
+  if (grow(h->links, lb) != cudaSuccess) return fail(OV_ERR_NOMEM);
+  const int nb = (int)((V + 127) / 128);
+  if (h->prec == OV_PREC_FP64)
+    k_links<double2><<<nb, 128, 0, h->st>>>(h->g, h->antiperiodic, src, (double2*)h->links.p);
+  else
+    k_links<float2><<<nb, 128, 0, h->st>>>(h->g, h->antiperiodic, src, (float2*)h->links.p);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->st) != cudaSuccess) return fail(OV_ERR_CUDA);
+  release(tmp);
+  *hp = h;
+  return OV_OK;
+}
+
+extern "C" void ov_destroy(ov_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  if (h->st) cudaStreamSynchronize(h->st);
+  Buf* all[] = {&h->links, &h->xcanon, &h->ycanon, &h->tv, &h->tw, &h->p, &h->r, &h->vring, &h->wring, &h->yacc,
+                &h->coef_alp, &h->coef_bet, &h->coef_gam, &h->coef_nv, &h->coef_nw, &h->coef_status,
+                &h->coef_kbreak, &h->partials, &h->counters, &h->scale, &h->iQ, &h->iT, &h->ileff, &h->iS, &h->is,
+                &h->irh_its, &h->irh_ok, &h->iperm, &h->ifail, &h->ck, &h->cl, &h->ckprev, &h->cc_cur, &h->cc_prev,
+                &h->cc_fin, &h->cacc_cur, &h->cacc_fin, &h->c_est_in, &h->c_est_out, &h->c_rhst, &h->c_rhit,
+                &h->vptr};
+  for (Buf* b : all) release(*b);
+  for (Buf& b : h->chunks) release(b);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+}
+
+// ---------------------------------------------------------------- workspace
+static int ensure_outer(ov_handle* h, int nrhs, int ld) {
+  const size_t vb = vec_bytes(h) * nrhs;
+  CK(grow(h->tv, vb));
+  CK(grow(h->tw, vb));
+  CK(grow(h->p, vb));
+  CK(grow(h->r, vb));
+  CK(grow(h->vring, 2 * vb));
+  CK(grow(h->wring, 2 * vb));
+  const size_t cb = sizeof(double2) * (size_t)nrhs * ld;
+  CK(grow(h->coef_alp, cb));
+  CK(grow(h->coef_bet, cb));
+  CK(grow(h->coef_gam, cb));
+  CK(grow(h->coef_nw, cb));
+  CK(grow(h->coef_nv, sizeof(double) * (size_t)nrhs * ld));
+  CK(grow(h->coef_status, sizeof(int) * nrhs));
+  CK(grow(h->coef_kbreak, sizeof(int) * nrhs));
+  CK(grow(h->partials, sizeof(double) * 4 * (size_t)nrhs * num_site_blocks(h->g)));
+  if (h->counters.bytes < sizeof(unsigned) * nrhs) {
+    CK(grow(h->counters, sizeof(unsigned) * nrhs));
+    CK(cudaMemsetAsync(h->counters.p, 0, sizeof(unsigned) * nrhs, h->st));
+  }
+  CK(grow(h->scale, sizeof(double) * nrhs));
+  h->cap_rhs = nrhs;
+  h->cap_ld = ld;
+  return OV_OK;
+}
+
+static int ensure_inner(ov_handle* h, int count, int ld) {
+  // ld: leading dimension of the per-problem k-vectors (>= k + 2)
+  CK(grow(h->iQ, sizeof(double2) * (size_t)count * ld * kMaxL));
+  CK(grow(h->iT, sizeof(double2) * (size_t)count * kMaxL * 3));
+  CK(grow(h->ileff, sizeof(int) * count));
+  CK(grow(h->iS, sizeof(double2) * (size_t)2 * count * kMaxL * kMaxL));
+  CK(grow(h->is, sizeof(double2) * (size_t)2 * count * kMaxL));
+  CK(grow(h->irh_its, sizeof(int) * 2 * count));
+  CK(grow(h->irh_ok, sizeof(int) * 2 * count));
+  CK(grow(h->iperm, sizeof(int) * 2 * (size_t)count * kMaxL));
+  CK(grow(h->ifail, sizeof(int) * count));
+  const size_t cb = sizeof(double2) * (size_t)count * ld;
+  CK(grow(h->ck, sizeof(int) * count));
+  CK(grow(h->cl, sizeof(int) * count));
+  CK(grow(h->ckprev, sizeof(int) * count));
+  CK(grow(h->cc_cur, cb));
+  CK(grow(h->cc_prev, cb));
+  CK(grow(h->cc_fin, cb));
+  const size_t ab = acc_elem_bytes(h->prec) * (size_t)count * ld;
+  CK(grow(h->cacc_cur, ab));
+  CK(grow(h->cacc_fin, ab));
+  CK(grow(h->c_est_in, sizeof(double) * count));
+  CK(grow(h->c_est_out, sizeof(double) * count));
+  CK(grow(h->c_rhst, sizeof(int) * count));
+  CK(grow(h->c_rhit, sizeof(int) * count));
+  h->inner_cap = count;
+  h->inner_ld = ld;
+  return OV_OK;
+}
+
+static InnerWork inner_work(ov_handle* h) {
+  InnerWork w;
+  w.Q = (double2*)h->iQ.p;
+  w.T = (double2*)h->iT.p;
+  w.leff = (int*)h->ileff.p;
+  w.S = (double2*)h->iS.p;
+  w.s = (double2*)h->is.p;
+  w.rh_its = (int*)h->irh_its.p;
+  w.rh_ok = (int*)h->irh_ok.p;
+  w.perm = (int*)h->iperm.p;
+  w.fail = (int*)h->ifail.p;
+  w.ld = h->inner_ld;  // Q rows per problem, as allocated by ensure_inner
+  return w;
+}
+
+static Coefs coefs(ov_handle* h, int ld) {
+  Coefs c;
+  c.alp = (double2*)h->coef_alp.p;
+  c.bet = (double2*)h->coef_bet.p;
+  c.gam = (double2*)h->coef_gam.p;
+  c.nv = (double*)h->coef_nv.p;
+  c.nw = (double2*)h->coef_nw.p;
+  c.status = (int*)h->coef_status.p;
+  c.kbreak = (int*)h->coef_kbreak.p;
+  c.ld = ld;
+  return c;
+}
+
+// pointer to basis slot `slot` (0-based, = step j - 1), allocating chunks on demand
+static int basis_slot(ov_handle* h, int nrhs, int slot, void** out) {
+  if (h->chunk_rhs != nrhs) {
+    for (Buf& b : h->chunks) release(b);
+    h->chunks.clear();
+    h->chunk_rhs = nrhs;
+  }
+  const int c = slot / kChunk;
+  while ((int)h->chunks.size() <= c) {
+    Buf b;
+    cudaError_t e = grow(b, vec_bytes(h) * nrhs * kChunk);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // clear the allocation error
+      return OV_ERR_NOMEM;
+    }
+    h->chunks.push_back(b);
+  }
+  *out = (char*)h->chunks[c].p + vec_bytes(h) * nrhs * (size_t)(slot % kChunk);
+  return OV_OK;
+}
+
+// ---------------------------------------------------------------- sign apply
+static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,
+                           ov_info* info, int add_x) {
+  if (!h || !x || !y || nrhs < 1 || k_max < 1 || l < 1 || !(tol >= 0.0)) return OV_ERR_ARG;
+  if (mem != OV_MEM_HOST && mem != OV_MEM_DEVICE) return OV_ERR_ARG;
+  if (l > kMaxL) return OV_ERR_TOO_LARGE;
+  const ov_opts& o = h->o;
+  const int ktarget = o.k_fixed > 0 ? o.k_fixed : k_max;
+  if (ktarget > kMaxInnerK) return OV_ERR_TOO_LARGE;
+  CK(cudaSetDevice(h->dev));
+  cudaStream_t st = h->st;
+  const Geometry& g = h->g;
+  const bool herm = h->mu == 0.0;
+  const int mode = herm ? kModeLanczos : kModeTwoSided;
+  const int ld = ktarget + 2;
+  int rc = ensure_outer(h, nrhs, ld);
+  if (rc != OV_OK) return rc;
+  rc = ensure_inner(h, nrhs, ld);
+  if (rc != OV_OK) return rc;
+  const size_t n12 = 12 * (size_t)g.V;
+  const size_t canon = sizeof(double2) * n12 * nrhs;
+  const double2* xd = (const double2*)x;
+  double2* yd = (double2*)y;
+  if (mem == OV_MEM_HOST) {
+    CK(grow(h->xcanon, canon));
+    CK(grow(h->ycanon, canon));
+    CK(cudaMemcpyAsync(h->xcanon.p, x, canon, cudaMemcpyHostToDevice, st));
+    xd = (const double2*)h->xcanon.p;
+    yd = (double2*)h->ycanon.p;
+  }
+  Coefs c = coefs(h, ld);
+  const size_t vb1 = vec_bytes(h);
+  const size_t vbn = vb1 * nrhs;
+  CK(cudaMemsetAsync(c.alp, 0, sizeof(double2) * (size_t)nrhs * ld, st));
+  CK(cudaMemsetAsync(c.bet, 0, sizeof(double2) * (size_t)nrhs * ld, st));
+  CK(cudaMemsetAsync(c.gam, 0, sizeof(double2) * (size_t)nrhs * ld, st));
+  CK(cudaMemsetAsync(h->vring.p, 0, 2 * vbn, st));
+  CK(cudaMemsetAsync(h->wring.p, 0, 2 * vbn, st));
+  // v_1 = w_1 = x / ||x||: x goes to tv (and tw), the norm into nv_1 / nw_1
+  CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 1, st));
+  if (!herm) CK(cudaMemcpyAsync(h->tw.p, h->tv.p, vbn, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpy2DAsync(h->scale.p, sizeof(double), (double*)c.nv + 1, sizeof(double) * ld, sizeof(double), nrhs,
+                       cudaMemcpyDeviceToDevice, st));
+  h->stats.launches += 1;
+  h->stats.other_launches += 1;
+  const int t_total = tstart(h, kClsTotal);
+
+  int recomb = o.recombination;
+  if (recomb == OV_RECOMB_AUTO) {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    const size_t need = vbn * (size_t)ktarget;
+    recomb = need + ((size_t)2 << 30) < fr ? OV_RECOMB_STORED : OV_RECOMB_TWO_PASS;
+  }
+
+  StepArgs a{};
+  a.g = g;
+  a.nrhs = nrhs;
+  a.links = h->links.p;
+  a.mass = h->m_w + 4.0;
+  a.emu = exp(h->mu);
+  a.emui = exp(-h->mu);
+  a.tv = h->tv.p;
+  a.tw = h->tw.p;
+  a.p = h->p.p;
+  a.r = h->r.p;
+  a.s_tv = a.s_tw = a.s_p = a.s_r = n12;
+  a.s_vprev = a.s_vcur = a.s_wprev = a.s_wcur = n12;
+  a.c = c;
+  a.breakdown_tol = o.breakdown_tol;
+  a.partials = (double*)h->partials.p;
+  a.counters = (unsigned*)h->counters.p;
+
+  // host-side per-RHS state
+  std::vector<int> done(nrhs, 0), kfin(nrhs, 0), lfin(nrhs, 0), itfin(nrhs, 0), stat(nrhs, OV_OK);
+  std::vector<int> kprev(nrhs, 0), kcur(nrhs, 0), lreq(nrhs, std::min(l, kMaxL));
+  std::vector<double> estfin(nrhs, INFINITY), estin(nrhs, NAN);
+  std::vector<int> dstatus(nrhs), dkbreak(nrhs), rhst(nrhs), rhit(nrhs), leff(nrhs);
+  std::vector<double> eo(nrhs), ei(nrhs);
+  std::vector<void*> slots;  // device pointer of each stored v_j (stored mode)
+  CK(cudaMemcpyAsync(h->cl.p, lreq.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(h->cc_fin.p, 0, sizeof(double2) * (size_t)nrhs * ld, st));
+  CK(cudaMemsetAsync(h->cacc_fin.p, 0, acc_elem_bytes(h->prec) * (size_t)nrhs * ld, st));
+  InnerWork iw = inner_work(h);
+  int ndone = 0;
+  int j = 0;
+  void* prev_v = (char*)h->vring.p + vbn;  // zero slot: v_0
+  const int first = o.first_check > 0 ? o.first_check : o.check_interval;
+  for (j = 1; j <= ktarget && ndone < nrhs; ++j) {
+    void* vcur = nullptr;
+    if (recomb == OV_RECOMB_STORED) {
+      rc = basis_slot(h, nrhs, j - 1, &vcur);
+      if (rc != OV_OK) {
+        if (o.recombination != OV_RECOMB_AUTO) return rc;
+        recomb = OV_RECOMB_TWO_PASS;  // out of memory: fall back to the double pass
+      }
+    }
+    if (recomb != OV_RECOMB_STORED) vcur = (char*)h->vring.p + vbn * ((j - 1) % 2);
+    if (recomb == OV_RECOMB_STORED) slots.push_back(vcur);
+    a.j = j;
+    a.vprev = prev_v;
+    a.vcur = vcur;
+    a.wprev = (char*)h->wring.p + vbn * (j % 2);
+    a.wcur = (char*)h->wring.p + vbn * ((j - 1) % 2);
+    if (j == 1) {
+      CK(cudaMemsetAsync((char*)h->wring.p + vbn, 0, vbn, st));
+    }
+    int ts = tstart(h, kClsStencil);
+    CK(launch_step(h->prec, mode, a, st));
+    tstop(h, ts);
+    ts = tstart(h, kClsUpdate);
+    CK(launch_update(h->prec, mode, a, st));
+    tstop(h, ts);
+    h->stats.launches += 2;
+    h->stats.stencil_launches += 1;
+    h->stats.update_launches += 1;
+    h->stats.outer_steps += 1;
+    prev_v = vcur;
+    const bool fixed = o.k_fixed > 0;
+    const bool check = fixed ? (j == ktarget) : ((j >= first && (j - first) % o.check_interval == 0) || j == ktarget);
+    if (!check) continue;
+    // read the breakdown state first: a Lanczos breakdown fixes k for that RHS
+    CK(cudaMemcpyAsync(dstatus.data(), c.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(dkbreak.data(), c.kbreak, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int r = 0; r < nrhs; ++r) kcur[r] = (dstatus[r] != kStOK && dkbreak[r] > 0) ? std::min(dkbreak[r], j) : j;
+    CK(cudaMemcpyAsync(h->ck.p, kcur.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->ckprev.p, kprev.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    const int ti = tstart(h, kClsInner);
+    cudaError_t e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, ld, iw,
+                              o.rh_tol, o.rh_maxit, o.inner_dl, (double2*)h->cc_cur.p, ld, h->cacc_cur.p, h->prec,
+                              (double*)h->c_est_in.p, (const double2*)h->cc_prev.p, ld, (const int*)h->ckprev.p,
+                              (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, st);
+    CK(e);
+    tstop(h, ti);
+    h->stats.launches += 3;
+    h->stats.inner_launches += 3;
+    h->stats.checks += 1;
+    CK(cudaMemcpyAsync(eo.data(), h->c_est_out.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ei.data(), h->c_est_in.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rhst.data(), h->c_rhst.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rhit.data(), h->c_rhit.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(leff.data(), h->ileff.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int r = 0; r < nrhs; ++r) {
+      if (done[r]) continue;
+      int fin = 0, sr = OV_OK;
+      double est = eo[r];
+      const bool lucky = dstatus[r] == kStLucky;
+      const bool broke = dstatus[r] == kStBreakdown;
+      if (dstatus[r] == kStZero) {
+        // zero source: y = 0 exactly, nothing to iterate
+        done[r] = 1;
+        ++ndone;
+        kfin[r] = 0;
+        estfin[r] = 0.0;
+        estin[r] = 0.0;
+        stat[r] = OV_OK;
+        continue;
+      }
+      if (rhst[r] != 0) {
+        fin = 1;
+        sr = OV_ERR_RH_NOCONV;
+      } else if (broke) {
+        fin = 1;
+        sr = OV_ERR_BREAKDOWN;
+      } else if (fixed) {
+        fin = 1;
+        est = NAN;
+      } else {
+        if (lucky) est = 0.0;
+        if (est <= tol || lucky || j == ktarget) {
+          fin = 1;
+          est = std::max(est, ei[r]);
+          sr = est <= tol ? OV_OK : OV_NOT_CONVERGED;
+        }
+      }
+      if (fin) {
+        done[r] = 1;
+        ++ndone;
+        kfin[r] = kcur[r];
+        lfin[r] = leff[r];
+        itfin[r] = rhit[r];
+        estfin[r] = est;
+        estin[r] = ei[r];
+        stat[r] = sr;
+        CK(cudaMemcpyAsync((double2*)h->cc_fin.p + (size_t)r * ld, (double2*)h->cc_cur.p + (size_t)r * ld,
+                           sizeof(double2) * ld, cudaMemcpyDeviceToDevice, st));
+        const size_t ab = acc_elem_bytes(h->prec);
+        CK(cudaMemcpyAsync((char*)h->cacc_fin.p + ab * (size_t)r * ld, (char*)h->cacc_cur.p + ab * (size_t)r * ld,
+                           ab * ld, cudaMemcpyDeviceToDevice, st));
+      } else {
+        kprev[r] = kcur[r];
+      }
+    }
+    std::swap(h->cc_cur, h->cc_prev);
+  }
+  const int kmax_used = *std::max_element(kfin.begin(), kfin.end());
+  // recombination
+  CK(cudaMemcpyAsync(h->ck.p, kfin.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+  const int tr = tstart(h, kClsRecomb);
+  if (recomb == OV_RECOMB_STORED) {
+    CK(grow(h->vptr, sizeof(void*) * std::max<size_t>(slots.size(), 1)));
+    CK(cudaMemcpyAsync(h->vptr.p, slots.data(), sizeof(void*) * slots.size(), cudaMemcpyHostToDevice, st));
+    CK(launch_recombine(h->prec, g, nrhs, (const void* const*)h->vptr.p, n12, h->cacc_fin.p, ld,
+                        (const int*)h->ck.p, (const double*)h->scale.p, xd, add_x, yd, st));
+    h->stats.launches += 1;
+    h->stats.other_launches += 1;
+  } else {
+    // second pass: regenerate v_j from the stored coefficients and accumulate y += c_j v_j
+    const size_t ab = acc_elem_bytes(h->prec) * n12 * nrhs;
+    CK(grow(h->yacc, ab));
+    CK(cudaMemsetAsync(h->yacc.p, 0, ab, st));
+    CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, st));
+    CK(cudaMemsetAsync(h->vring.p, 0, 2 * vbn, st));
+    StepArgs b = a;
+    b.yacc = h->yacc.p;
+    b.s_yacc = n12;
+    b.s_tnext = n12;
+    b.cacc = h->cacc_fin.p;
+    void* tcur = h->tv.p;
+    void* tnxt = h->p.p;
+    void* vprev2 = (char*)h->vring.p + vbn;
+    for (int jj = 1; jj <= kmax_used; ++jj) {
+      void* vc = (char*)h->vring.p + vbn * ((jj - 1) % 2);
+      b.j = jj;
+      b.tv = tcur;
+      b.tnext = tnxt;
+      b.vprev = vprev2;
+      b.vcur = vc;
+      CK(launch_step(h->prec, kModeRegen, b, st));
+      std::swap(tcur, tnxt);
+      vprev2 = vc;
+    }
+    CK(launch_finish_acc(h->prec, g, nrhs, h->yacc.p, n12, (const double*)h->scale.p, xd, add_x, yd, st));
+    h->stats.launches += kmax_used + 2;
+    h->stats.stencil_launches += kmax_used;
+    h->stats.regen_steps += kmax_used;
+    h->stats.other_launches += 2;
+  }
+  tstop(h, tr);
+  tstop(h, t_total);
+  if (mem == OV_MEM_HOST) CK(cudaMemcpyAsync(y, yd, canon, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  tcollect(h);
+  int worst = OV_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    if (info) {
+      info[r].k = kfin[r];
+      info[r].l = lfin[r];
+      info[r].rh_iters = itfin[r];
+      info[r].status = stat[r];
+      info[r].err_est = estfin[r];
+      info[r].err_inner = estin[r];
+    }
+    if (stat[r] < 0 && (worst >= 0 || stat[r] < worst)) worst = stat[r];
+    else if (worst == OV_OK && stat[r] > 0) worst = stat[r];
+  }
+  return worst;
+}
+
+extern "C" int ov_sign_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,
+                             ov_info* info) {
+  return sign_apply_impl(h, nrhs, x, y, mem, tol, k_max, l, info, 0);
+}
+
+extern "C" int ov_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,
+                        ov_info* info) {
+  return sign_apply_impl(h, nrhs, x, y, mem, tol, k_max, l, info, 1);
+}
+
+// ---------------------------------------------------------------- stencil alone
+extern "C" int ov_wilson_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, int dagger) {
+  if (!h || !x || !y || nrhs < 1) return OV_ERR_ARG;
+  if (mem != OV_MEM_HOST && mem != OV_MEM_DEVICE) return OV_ERR_ARG;
+  CK(cudaSetDevice(h->dev));
+  cudaStream_t st = h->st;
+  const Geometry& g = h->g;
+  int rc = ensure_outer(h, nrhs, std::max(h->cap_ld, 4));
+  if (rc != OV_OK) return rc;
+  const size_t n12 = 12 * (size_t)g.V;
+  const size_t canon = sizeof(double2) * n12 * nrhs;
+  const double2* xd = (const double2*)x;
+  double2* yd = (double2*)y;
+  if (mem == OV_MEM_HOST) {
+    CK(grow(h->xcanon, canon));
+    CK(grow(h->ycanon, canon));
+    CK(cudaMemcpyAsync(h->xcanon.p, x, canon, cudaMemcpyHostToDevice, st));
+    xd = (const double2*)h->xcanon.p;
+    yd = (double2*)h->ycanon.p;
+  }
+  Coefs c = coefs(h, h->cap_ld);
+  CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, st));
+  StepArgs a{};
+  a.g = g;
+  a.nrhs = nrhs;
+  a.links = h->links.p;
+  a.mass = h->m_w + 4.0;
+  a.emu = exp(h->mu);
+  a.emui = exp(-h->mu);
+  a.tv = h->tv.p;
+  a.p = h->p.p;
+  a.s_tv = a.s_p = n12;
+  a.dagger = dagger ? 1 : 0;
+  a.c = c;
+  CK(launch_step(h->prec, kModeApply, a, st));
+  CK(launch_unpack(h->prec, g, nrhs, h->p.p, n12, yd, st));
+  if (mem == OV_MEM_HOST) CK(cudaMemcpyAsync(y, yd, canon, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return OV_OK;
+}
+
+// ---------------------------------------------------------------- inner level alone
+extern "C" int ov_inner_sign(ov_handle* h, int count, int ld, const int* k, const void* alpha, const void* beta,
+                             const void* gamma, int hermitian, int l, void* cout, double* est_inner, int* rh_iters) {
+  if (!h || count < 1 || !k || !alpha || !beta || !gamma || !cout || l < 1) return OV_ERR_ARG;
+  if (ld < 1) return OV_ERR_ARG;
+  if (l > kMaxL || ld > kMaxInnerK) return OV_ERR_TOO_LARGE;
+  for (int i = 0; i < count; ++i)
+    if (k[i] < 1 || k[i] > ld) return OV_ERR_ARG;
+  CK(cudaSetDevice(h->dev));
+  cudaStream_t st = h->st;
+  const int ldi = ld + 2;
+  int rc = ensure_inner(h, count, ldi);
+  if (rc != OV_OK) return rc;
+  // coefficients in the 1-based layout of the outer level
+  std::vector<double2> A((size_t)count * ldi), B((size_t)count * ldi), G((size_t)count * ldi);
+  const double2* ai = (const double2*)alpha;
+  const double2* bi = (const double2*)beta;
+  const double2* gi = (const double2*)gamma;
+  for (int i = 0; i < count; ++i)
+    for (int jj = 0; jj < ld; ++jj) {
+      A[(size_t)i * ldi + jj + 1] = ai[(size_t)i * ld + jj];
+      B[(size_t)i * ldi + jj + 1] = bi[(size_t)i * ld + jj];
+      G[(size_t)i * ldi + jj + 1] = hermitian ? bi[(size_t)i * ld + jj] : gi[(size_t)i * ld + jj];
+    }
+  Buf dA, dB, dG;
+  auto cleanup = [&]() {
+    release(dA);
+    release(dB);
+    release(dG);
+  };
+  const size_t cb = sizeof(double2) * (size_t)count * ldi;
+  if (grow(dA, cb) != cudaSuccess || grow(dB, cb) != cudaSuccess || grow(dG, cb) != cudaSuccess) {
+    cleanup();
+    return OV_ERR_NOMEM;
+  }
+  std::vector<int> lv(count, l);
+  cudaMemcpyAsync(dA.p, A.data(), cb, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dB.p, B.data(), cb, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dG.p, G.data(), cb, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->ck.p, k, sizeof(int) * count, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(h->cl.p, lv.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st);
+  InnerWork iw = inner_work(h);
+  cudaError_t e = run_inner(count, (const int*)h->ck.p, (const int*)h->cl.p, hermitian ? 1 : 0, (double2*)dA.p,
+                            (double2*)dB.p, (double2*)dG.p, ldi, iw, h->o.rh_tol, h->o.rh_maxit, h->o.inner_dl,
+                            (double2*)h->cc_cur.p, ldi, nullptr, h->prec, (double*)h->c_est_in.p, nullptr, ldi,
+                            nullptr, nullptr, (int*)h->c_rhst.p, (int*)h->c_rhit.p, st);
+  std::vector<double2> C((size_t)count * ldi);
+  std::vector<double> ein(count);
+  std::vector<int> rs(count), ri(count);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(C.data(), h->cc_cur.p, cb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ein.data(), h->c_est_in.p, sizeof(double) * count, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rs.data(), h->c_rhst.p, sizeof(int) * count, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ri.data(), h->c_rhit.p, sizeof(int) * count, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "libov: ov_inner_sign: %s\n", cudaGetErrorString(e));
+    return OV_ERR_CUDA;
+  }
+  double2* co = (double2*)cout;
+  int worst = OV_OK;
+  for (int i = 0; i < count; ++i) {
+    for (int jj = 0; jj < ld; ++jj) co[(size_t)i * ld + jj] = jj < k[i] ? C[(size_t)i * ldi + jj + 1] : double2{0, 0};
+    if (est_inner) est_inner[i] = ein[i];
+    if (rh_iters) rh_iters[i] = ri[i];
+    if (rs[i] != 0) worst = OV_ERR_RH_NOCONV;
+  }
+  return worst;
+}
+
+extern "C" int ov_rh_sign(ov_handle* h, int count, int m, const void* T, void* S, int* iters) {
+  if (!h || count < 1 || m < 1 || !T || !S) return OV_ERR_ARG;
+  if (m > kMaxL) return OV_ERR_TOO_LARGE;
+  CK(cudaSetDevice(h->dev));
+  cudaStream_t st = h->st;
+  int rc = ensure_inner(h, (count + 1) / 2, std::max(h->inner_ld, 4));
+  if (rc != OV_OK) return rc;
+  const size_t mb = sizeof(double2) * (size_t)count * m * m;
+  Buf dT, dS, dI;
+  auto cleanup = [&]() {
+    release(dT);
+    release(dS);
+    release(dI);
+  };
+  if (grow(dT, mb) != cudaSuccess || grow(dS, mb) != cudaSuccess || grow(dI, sizeof(int) * 2 * count) != cudaSuccess) {
+    cleanup();
+    return OV_ERR_NOMEM;
+  }
+  InnerWork iw = inner_work(h);
+  cudaError_t e = cudaMemcpyAsync(dT.p, T, mb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = run_rh_dense(count, m, (const double2*)dT.p, (double2*)dS.p, (int*)dI.p, (int*)dI.p + count, h->o.rh_tol,
+                     h->o.rh_maxit, iw, st);
+  std::vector<int> it(2 * count);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S, dS.p, mb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(it.data(), dI.p, sizeof(int) * 2 * count, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "libov: ov_rh_sign: %s\n", cudaGetErrorString(e));
+    return OV_ERR_CUDA;
+  }
+  int worst = OV_OK;
+  for (int i = 0; i < count; ++i) {
+    if (iters) iters[i] = it[i];
+    if (!it[count + i]) worst = OV_ERR_RH_NOCONV;
+  }
+  return worst;
+}
+
+extern "C" int ov_version(char* buf, size_t len) {
+  if (!buf || len == 0) return OV_ERR_ARG;
+  int dev = 0;
+  cudaDeviceProp p;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+    snprintf(buf, len, "libov 0.1 (no device)");
+    return OV_ERR_CUDA;
+  }
+  snprintf(buf, len, "libov 0.1 sm_%d%d %s", p.major, p.minor, p.name);
+  return OV_OK;
+}

@@ -1,0 +1,581 @@
+// Inner level of the nested method, in double precision (Sec. 3, Eqs. (nested),
+// (precond); Sec. 2, Eq. (Roberts)).
+//
+//  k_inner   one CTA per problem: tridiagonal LU with partial pivoting of the Ritz
+//            matrix H_k (row interchanges between neighbouring rows only), then l steps
+//            of Lanczos (mu = 0) or two-sided Lanczos (mu != 0) on M = H_k + H_k^{-1}
+//            from e_1. M u = H u + H^{-1} u and M^dag w = H^dag w + H^{-dag} w both use
+//            the one factorisation (the solve with H^dag runs the factors backwards).
+//  k_rh      one CTA per matrix: Roberts-Higham S_{n+1} = (S_n + S_n^{-1})/2 with an
+//            in-place Gauss-Jordan inversion (partial pivoting) of the whole l x l
+//            matrix in shared memory (l <= 120 complex: 225 KB).
+//  k_combine one CTA per problem: c = Q_l s, the inner estimate against the leading
+//            (l - dl) block, the outer estimate against the previous check.
+#include <math.h>
+
+#include <algorithm>
+
+#include "ov_internal.h"
+#include "ov_types.cuh"
+
+namespace ov {
+
+constexpr int kInnerThreads = 256;
+
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double zabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+  // scaled to avoid overflow of |b|^2 for large |b|
+  double s = fmax(fabs(b.x), fabs(b.y));
+  if (s == 0.0) return make_double2(INFINITY, INFINITY);
+  double2 bs = make_double2(b.x / s, b.y / s), as = make_double2(a.x / s, a.y / s);
+  double d = bs.x * bs.x + bs.y * bs.y;
+  return make_double2((as.x * bs.x + as.y * bs.y) / d, (as.y * bs.x - as.x * bs.y) / d);
+}
+__device__ __forceinline__ double2 zinv(double2 b) { return zdiv(make_double2(1.0, 0.0), b); }
+
+// block sum over kInnerThreads threads; result returned to every thread
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+struct InnerSmem {
+  double2 *d, *a, *c;           // H diagonal, subdiagonal (row m, col m-1), superdiagonal (row m, col m+1)
+  double2 *uinv, *u1, *u2, *l;  // LU factors
+  unsigned char* sw;            // row interchange at step m
+  double2 *q, *qp, *w, *wp, *u, *z;
+  double* red;
+};
+
+// x = H^{-1} b with the GEPP factors (x may alias nothing; y is scratch of size k)
+__device__ void tri_solve(const InnerSmem& S, int k, const double2* b, double2* x) {
+  double2 cur = b[0];
+  for (int m = 0; m < k - 1; ++m) {
+    const double2 nb = b[m + 1];
+    if (!S.sw[m]) {
+      x[m] = cur;
+      cur = zsub(nb, zmul(S.l[m], cur));
+    } else {
+      x[m] = nb;
+      cur = zsub(cur, zmul(S.l[m], nb));
+    }
+  }
+  x[k - 1] = cur;
+  x[k - 1] = zmul(x[k - 1], S.uinv[k - 1]);
+  if (k >= 2) x[k - 2] = zmul(zsub(x[k - 2], zmul(S.u1[k - 2], x[k - 1])), S.uinv[k - 2]);
+  for (int m = k - 3; m >= 0; --m)
+    x[m] = zmul(zsub(zsub(x[m], zmul(S.u1[m], x[m + 1])), zmul(S.u2[m], x[m + 2])), S.uinv[m]);
+}
+
+// z = H^{-dag} b: H = E^{-1} U with E the product of the elimination steps, so
+// H^dag z = b  <=>  U^dag g = b, z = E_1^dag ... E_{k-1}^dag g.
+__device__ void tri_solve_dag(const InnerSmem& S, int k, const double2* b, double2* z) {
+  for (int m = 0; m < k; ++m) {
+    double2 t = b[m];
+    if (m >= 1) t = zsub(t, zmul(zconj(S.u1[m - 1]), z[m - 1]));
+    if (m >= 2) t = zsub(t, zmul(zconj(S.u2[m - 2]), z[m - 2]));
+    z[m] = zmul(t, zconj(S.uinv[m]));
+  }
+  for (int m = k - 2; m >= 0; --m) {
+    const double2 cl = zconj(S.l[m]);
+    const double2 gi = z[m], gn = z[m + 1];
+    if (!S.sw[m]) {
+      z[m] = zsub(gi, zmul(cl, gn));
+    } else {
+      z[m] = gn;
+      z[m + 1] = zsub(gi, zmul(cl, gn));
+    }
+  }
+}
+
+// LU with partial pivoting of the tridiagonal H (thread 0). Returns false if singular.
+__device__ bool tri_factor(const InnerSmem& S, int k) {
+  double2 dd = S.d[0];
+  double2 ee = k > 1 ? S.c[0] : make_double2(0.0, 0.0);
+  for (int m = 0; m < k - 1; ++m) {
+    const double2 an = S.a[m + 1], dn = S.d[m + 1];
+    const double2 cn = (m + 1 <= k - 2) ? S.c[m + 1] : make_double2(0.0, 0.0);
+    double2 r0, r1, r2, lm;
+    if (zabs2(dd) >= zabs2(an)) {
+      if (zabs2(dd) == 0.0) return false;
+      lm = zdiv(an, dd);
+      r0 = dd; r1 = ee; r2 = make_double2(0.0, 0.0);
+      dd = zsub(dn, zmul(lm, ee));
+      ee = cn;
+      S.sw[m] = 0;
+    } else {
+      lm = zdiv(dd, an);
+      r0 = an; r1 = dn; r2 = cn;
+      dd = zsub(ee, zmul(lm, dn));
+      ee = zscale(zmul(lm, cn), -1.0);
+      S.sw[m] = 1;
+    }
+    S.uinv[m] = zinv(r0);
+    S.u1[m] = r1;
+    S.u2[m] = r2;
+    S.l[m] = lm;
+  }
+  if (zabs2(dd) == 0.0) return false;
+  S.uinv[k - 1] = zinv(dd);
+  return true;
+}
+
+// y = H x (parallel)
+__device__ __forceinline__ void tri_mul(const InnerSmem& S, int k, const double2* x, double2* y, bool dag) {
+  for (int m = threadIdx.x; m < k; m += blockDim.x) {
+    double2 t;
+    if (!dag) {
+      t = zmul(S.d[m], x[m]);
+      if (m >= 1) t = zadd(t, zmul(S.a[m], x[m - 1]));
+      if (m + 1 < k) t = zadd(t, zmul(S.c[m], x[m + 1]));
+    } else {
+      // (H^dag)_{m,m} = conj d_m, (H^dag)_{m,m-1} = conj H_{m-1,m} = conj c_{m-1},
+      // (H^dag)_{m,m+1} = conj H_{m+1,m} = conj a_{m+1}
+      t = zmul(zconj(S.d[m]), x[m]);
+      if (m >= 1) t = zadd(t, zmul(zconj(S.c[m - 1]), x[m - 1]));
+      if (m + 1 < k) t = zadd(t, zmul(zconj(S.a[m + 1]), x[m + 1]));
+    }
+    y[m] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kInnerThreads) k_inner(const int* __restrict__ k_dev, const int* __restrict__ l_dev,
+                                                         int hermitian, const double2* __restrict__ alp,
+                                                         const double2* __restrict__ bet,
+                                                         const double2* __restrict__ gam, int ldc, InnerWork w) {
+  int* fail = w.fail;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int prob = blockIdx.x;
+  const int k = k_dev[prob];
+  const int l = min(l_dev[prob], k);
+  const int tid = threadIdx.x;
+  InnerSmem S;
+  {
+    double2* base = (double2*)smem;
+    S.d = base; S.a = base + k; S.c = base + 2 * k;
+    S.uinv = base + 3 * k; S.u1 = base + 4 * k; S.u2 = base + 5 * k; S.l = base + 6 * k;
+    S.q = base + 7 * k; S.qp = base + 8 * k; S.w = base + 9 * k; S.wp = base + 10 * k;
+    S.u = base + 11 * k; S.z = base + 12 * k;
+    S.red = (double*)(base + 13 * k);
+    S.sw = (unsigned char*)(S.red + 32);
+  }
+  const double2* al = alp + (size_t)prob * ldc;
+  const double2* be = bet + (size_t)prob * ldc;
+  const double2* ga = gam + (size_t)prob * ldc;
+  for (int m = tid; m < k; m += blockDim.x) {
+    double2 dm = al[m + 1];
+    double2 am = m >= 1 ? be[m + 1] : make_double2(0.0, 0.0);
+    double2 cm = m + 1 < k ? ga[m + 2] : make_double2(0.0, 0.0);
+    if (hermitian) { dm.y = 0.0; am.y = 0.0; cm = m + 1 < k ? make_double2(be[m + 2].x, 0.0) : cm; }
+    S.d[m] = dm; S.a[m] = am; S.c[m] = cm;
+    const double2 zero = make_double2(0.0, 0.0);
+    S.q[m] = m == 0 ? make_double2(1.0, 0.0) : zero;
+    S.w[m] = S.q[m];
+    S.qp[m] = zero; S.wp[m] = zero;
+  }
+  __syncthreads();
+  __shared__ int s_ok;
+  if (tid == 0) s_ok = tri_factor(S, k) ? 1 : 0;
+  __syncthreads();
+  if (!s_ok) {
+    if (tid == 0) { fail[prob] = 1; w.leff[prob] = 0; }
+    return;
+  }
+  double2* Q = w.Q + (size_t)prob * w.ld * kMaxL;
+  double2* T = w.T + (size_t)prob * kMaxL * 3;
+  double2 b_i = make_double2(0.0, 0.0), g_i = make_double2(0.0, 0.0);  // inner beta_i, gamma_i
+  int done = 0;
+  const double exhaust_tol = 1e-13;
+  for (int i = 0; i < l; ++i) {
+    for (int m = tid; m < k; m += blockDim.x) Q[(size_t)m * kMaxL + i] = S.q[m];
+    // u = M q = H q + H^{-1} q ; z = M^dag w (two-sided)
+    if (tid == 0) tri_solve(S, k, S.q, S.u);
+    if (!hermitian && tid == 32) tri_solve_dag(S, k, S.w, S.z);
+    __syncthreads();
+    double mq2 = 0.0;
+    for (int m = tid; m < k; m += blockDim.x) {
+      double2 t = zmul(S.d[m], S.q[m]);
+      if (m >= 1) t = zadd(t, zmul(S.a[m], S.q[m - 1]));
+      if (m + 1 < k) t = zadd(t, zmul(S.c[m], S.q[m + 1]));
+      t = zadd(t, S.u[m]);
+      mq2 += zabs2(t);
+      S.u[m] = zsub(t, hermitian ? zscale(S.qp[m], b_i.x) : zmul(g_i, S.qp[m]));  // p
+      if (!hermitian) {
+        double2 y = zmul(zconj(S.d[m]), S.w[m]);
+        if (m >= 1) y = zadd(y, zmul(zconj(S.c[m - 1]), S.w[m - 1]));
+        if (m + 1 < k) y = zadd(y, zmul(zconj(S.a[m + 1]), S.w[m + 1]));
+        y = zadd(y, S.z[m]);
+        S.z[m] = zsub(y, zmul(zconj(b_i), S.wp[m]));  // r
+      }
+    }
+    __syncthreads();
+    // alpha = w^dag p (q^dag p in the Hermitian case)
+    double are = 0.0, aim = 0.0;
+    for (int m = tid; m < k; m += blockDim.x) {
+      const double2 wm = hermitian ? S.q[m] : S.w[m];
+      const double2 pm = S.u[m];
+      are += wm.x * pm.x + wm.y * pm.y;
+      aim += wm.x * pm.y - wm.y * pm.x;
+    }
+    are = block_sum(are, S.red);
+    aim = hermitian ? 0.0 : block_sum(aim, S.red);
+    const double mqn = sqrt(block_sum(mq2, S.red));
+    const double2 a_i = make_double2(are, aim);
+    if (tid == 0) T[i * 3 + 0] = a_i;
+    done = i + 1;
+    if (i == l - 1) break;
+    // q~ = p - alpha q ; w~ = r - conj(alpha) w ; delta
+    double dre = 0.0, dim = 0.0, n2 = 0.0;
+    for (int m = tid; m < k; m += blockDim.x) {
+      const double2 qt = zsub(S.u[m], zmul(a_i, S.q[m]));
+      S.u[m] = qt;
+      if (hermitian) {
+        n2 += zabs2(qt);
+      } else {
+        const double2 wt = zsub(S.z[m], zmul(zconj(a_i), S.w[m]));
+        S.z[m] = wt;
+        dre += wt.x * qt.x + wt.y * qt.y;
+        dim += wt.x * qt.y - wt.y * qt.x;
+      }
+    }
+    double bn;
+    double2 gn;
+    if (hermitian) {
+      bn = sqrt(block_sum(n2, S.red));
+      gn = make_double2(bn, 0.0);
+    } else {
+      dre = block_sum(dre, S.red);
+      dim = block_sum(dim, S.red);
+      const double ad = sqrt(dre * dre + dim * dim);
+      bn = sqrt(ad);
+      gn = bn > 0.0 ? make_double2(dre / bn, dim / bn) : make_double2(0.0, 0.0);
+    }
+    if (!(bn > exhaust_tol * mqn)) break;  // inner space exhausted: T_i is exact
+    if (tid == 0) {
+      T[(i + 1) * 3 + 1] = make_double2(bn, 0.0);
+      T[(i + 1) * 3 + 2] = gn;
+    }
+    const double2 wdiv = zinv(zconj(gn));
+    __syncthreads();
+    for (int m = tid; m < k; m += blockDim.x) {
+      S.qp[m] = S.q[m];
+      S.q[m] = zscale(S.u[m], 1.0 / bn);
+      if (!hermitian) {
+        S.wp[m] = S.w[m];
+        S.w[m] = zmul(S.z[m], wdiv);
+      }
+    }
+    b_i = make_double2(bn, 0.0);
+    g_i = gn;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    w.leff[prob] = done;
+    T[0 * 3 + 1] = make_double2(0.0, 0.0);
+    T[0 * 3 + 2] = make_double2(0.0, 0.0);
+    fail[prob] = 0;
+  }
+}
+
+// ------------------------------------------------------------ Roberts-Higham
+// CTA `m2` handles matrix m2: problems [0, count) are T_{leff}, [count, 2 count) are
+// T_{leff - dl} (the inner estimate); dense mode reads full matrices.
+template <bool CPLX>
+struct RhElem;
+template <> struct RhElem<true> { using T = double2; };
+template <> struct RhElem<false> { using T = double; };
+
+__device__ __forceinline__ double2 rz(double2 a) { return a; }
+__device__ __forceinline__ double el_abs2(double a) { return a * a; }
+__device__ __forceinline__ double el_abs2(double2 a) { return zabs2(a); }
+__device__ __forceinline__ double el_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ double2 el_mul(double2 a, double2 b) { return zmul(a, b); }
+__device__ __forceinline__ double el_sub(double a, double b) { return a - b; }
+__device__ __forceinline__ double2 el_sub(double2 a, double2 b) { return zsub(a, b); }
+__device__ __forceinline__ double el_inv(double a) { return 1.0 / a; }
+__device__ __forceinline__ double2 el_inv(double2 a) { return zinv(a); }
+__device__ __forceinline__ double el_avg(double a, double b) { return 0.5 * (a + b); }
+__device__ __forceinline__ double2 el_avg(double2 a, double2 b) { return make_double2(0.5 * (a.x + b.x), 0.5 * (a.y + b.y)); }
+__device__ __forceinline__ double el_from(double2 a) { return a.x; }
+__device__ __forceinline__ double2 el_from2(double2 a) { return a; }
+__device__ __forceinline__ double2 el_to2(double a) { return make_double2(a, 0.0); }
+__device__ __forceinline__ double2 el_to2(double2 a) { return a; }
+__device__ __forceinline__ double el_zero(double) { return 0.0; }
+__device__ __forceinline__ double2 el_zero(double2) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double el_one(double) { return 1.0; }
+__device__ __forceinline__ double2 el_one(double2) { return make_double2(1.0, 0.0); }
+__device__ __forceinline__ bool el_finite(double a) { return isfinite(a); }
+__device__ __forceinline__ bool el_finite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+template <class E>
+__device__ __forceinline__ E el_load(const double2* p) {
+  if constexpr (sizeof(E) == sizeof(double)) return p->x; else return *(const E*)p;
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(1024) k_rh(int count, int dense_m, const double2* __restrict__ dense_T,
+                                             InnerWork w, int dl, double rh_tol, int rh_maxit) {
+  using E = typename RhElem<CPLX>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int mid = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  int m;
+  if (dense_m > 0) {
+    m = dense_m;
+  } else {
+    const int prob = mid % count;
+    const int le = w.leff[prob];
+    m = mid < count ? le : le - dl;
+  }
+  if (m <= 0) {
+    if (tid == 0) { w.rh_ok[mid] = m == 0 ? 0 : 1; w.rh_its[mid] = 0; }
+    return;
+  }
+  E* W = (E*)smem;                    // m x m working matrix
+  E* col = W + (size_t)m * m;         // column buffer / reduction scratch
+  double* red = (double*)col;
+  int* piv_slot = (int*)col;
+  double2* Sg = w.S + (size_t)mid * kMaxL * kMaxL;  // global S_n (row-major, leading dim m)
+  int* perm = w.perm + (size_t)mid * kMaxL;
+  // S_0 = T
+  for (int e = tid; e < m * m; e += nth) {
+    const int i = e / m, j = e % m;
+    double2 v = make_double2(0.0, 0.0);
+    if (dense_m > 0) {
+      v = dense_T[(size_t)mid * m * m + e];
+    } else {
+      const double2* T = w.T + (size_t)(mid % count) * kMaxL * 3;
+      if (i == j) v = T[i * 3 + 0];
+      else if (i == j + 1) v = T[i * 3 + 1];      // subdiagonal beta_{i}
+      else if (j == i + 1) v = T[j * 3 + 2];      // superdiagonal gamma_{j}
+    }
+    if (!CPLX) v.y = 0.0;
+    Sg[e] = v;
+  }
+  __syncthreads();
+  int ok = 0, it = 0;
+  for (it = 1; it <= rh_maxit; ++it) {
+    for (int e = tid; e < m * m; e += nth) W[e] = el_load<E>(&Sg[e]);
+    __syncthreads();
+    bool singular = false;
+    for (int j = 0; j < m; ++j) {
+      // pivot search in column j (warp 0; ties keep the smaller row)
+      if (tid < 32) {
+        double best = -1.0;
+        int bi = j;
+        for (int i = j + tid; i < m; i += 32) {
+          const double a2 = el_abs2(W[(size_t)i * m + j]);
+          if (a2 > best) { best = a2; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (tid == 0) piv_slot[0] = best > 0.0 ? bi : -1;
+      }
+      __syncthreads();
+      const int p = piv_slot[0];
+      __syncthreads();
+      if (p < 0) { singular = true; break; }
+      if (p != j)
+        for (int c = tid; c < m; c += nth) {
+          const E t = W[(size_t)j * m + c];
+          W[(size_t)j * m + c] = W[(size_t)p * m + c];
+          W[(size_t)p * m + c] = t;
+        }
+      if (tid == 0) perm[j] = p;
+      __syncthreads();
+      const E inv = el_inv(W[(size_t)j * m + j]);
+      __syncthreads();
+      for (int c = tid; c < m; c += nth) W[(size_t)j * m + c] = c == j ? inv : el_mul(W[(size_t)j * m + c], inv);
+      for (int i = tid; i < m; i += nth) col[i] = i == j ? el_zero(inv) : W[(size_t)i * m + j];
+      __syncthreads();
+      for (int i = tid; i < m; i += nth)
+        if (i != j) W[(size_t)i * m + j] = el_zero(inv);
+      __syncthreads();
+      for (int e = tid; e < m * m; e += nth) {
+        const int i = e / m;
+        if (i == j) continue;
+        const int c = e - i * m;
+        W[e] = el_sub(W[e], el_mul(col[i], W[(size_t)j * m + c]));
+      }
+      __syncthreads();
+    }
+    if (singular) { ok = 0; break; }
+    // undo the row interchanges as column interchanges, last first
+    for (int j = m - 1; j >= 0; --j) {
+      const int p = perm[j];
+      if (p != j)
+        for (int i = tid; i < m; i += nth) {
+          const E t = W[(size_t)i * m + j];
+          W[(size_t)i * m + j] = W[(size_t)i * m + p];
+          W[(size_t)i * m + p] = t;
+        }
+      __syncthreads();
+    }
+    // S_{n+1} = (S_n + S_n^{-1}) / 2 ; convergence test in the Frobenius norm
+    double dif = 0.0, nrm = 0.0;
+    bool fin = true;
+    for (int e = tid; e < m * m; e += nth) {
+      const E sn = el_load<E>(&Sg[e]);
+      const E s1 = el_avg(sn, W[e]);
+      fin = fin && el_finite(s1);
+      dif += el_abs2(el_sub(s1, sn));
+      nrm += el_abs2(s1);
+      Sg[e] = el_to2(s1);
+    }
+    __syncthreads();
+    dif = warp_sum(dif);
+    nrm = warp_sum(nrm);
+    const int fin_all = __syncthreads_and(fin ? 1 : 0);
+    if ((tid & 31) == 0) { red[(tid >> 5) * 2] = dif; red[(tid >> 5) * 2 + 1] = nrm; }
+    __syncthreads();
+    double D = 0.0, N = 0.0;
+    for (int q = 0; q < (nth >> 5); ++q) { D += red[2 * q]; N += red[2 * q + 1]; }
+    __syncthreads();
+    if (!fin_all || !isfinite(D) || !isfinite(N)) { ok = 0; break; }
+    if (sqrt(D) <= rh_tol * sqrt(N)) { ok = 1; break; }
+  }
+  if (tid == 0) {
+    w.rh_ok[mid] = ok;
+    w.rh_its[mid] = it > rh_maxit ? rh_maxit : it;
+  }
+  for (int i = tid; i < m; i += nth) w.s[(size_t)mid * kMaxL + i] = Sg[(size_t)i * m];
+}
+
+// ------------------------------------------------------------ combine
+__global__ void __launch_bounds__(kInnerThreads) k_combine(int count, const int* __restrict__ k_dev,
+                                                           const int* __restrict__ l_dev, InnerWork w, int dl,
+                                                           double2* c, int ldo, void* cacc, int prec,
+                                                           double* est_inner, const double2* cprev, int ldp,
+                                                           const int* kprev_dev, double* est_outer, int* rh_status,
+                                                           int* rh_iters) {
+  const int* fail = w.fail;
+  __shared__ double red[32];
+  const int prob = blockIdx.x;
+  const int k = k_dev[prob];
+  const int le = w.leff[prob];
+  const int le2 = le - dl;
+  const int tid = threadIdx.x;
+  const double2* Q = w.Q + (size_t)prob * w.ld * kMaxL;
+  const double2* s1 = w.s + (size_t)prob * kMaxL;
+  const double2* s2 = w.s + (size_t)(count + prob) * kMaxL;
+  const bool bad = fail[prob] != 0 || le <= 0 || !w.rh_ok[prob];
+  // the inner space is exact when it was exhausted early or spans all of C^k
+  const bool exact = le >= k || le < min(l_dev[prob], k);
+  double nc = 0.0, nd = 0.0, no = 0.0;
+  const int kp = kprev_dev ? kprev_dev[prob] : 0;
+  // entries k+1 .. ldo-1 are cleared so that a shorter c never carries stale values
+  for (int m = k + tid; m < ldo - 1; m += blockDim.x) {
+    c[(size_t)prob * ldo + m + 1] = make_double2(0.0, 0.0);
+    if (cacc) {
+      if (prec == OV_PREC_FP64) ((double2*)cacc)[(size_t)prob * ldo + m + 1] = make_double2(0.0, 0.0);
+      else ((float4*)cacc)[(size_t)prob * ldo + m + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  for (int m = tid; m < k; m += blockDim.x) {
+    double2 v = make_double2(0.0, 0.0), v2 = make_double2(0.0, 0.0);
+    if (!bad) {
+      for (int i = 0; i < le; ++i) {
+        const double2 qv = Q[(size_t)m * kMaxL + i];
+        v = zadd(v, zmul(qv, s1[i]));
+        if (i < le2) v2 = zadd(v2, zmul(qv, s2[i]));
+      }
+    }
+    c[(size_t)prob * ldo + m + 1] = v;
+    if (cacc) {
+      if (prec == OV_PREC_FP64) {
+        ((double2*)cacc)[(size_t)prob * ldo + m + 1] = v;
+      } else {
+        const df64 re = df_from_double(v.x), im = df_from_double(v.y);
+        ((float4*)cacc)[(size_t)prob * ldo + m + 1] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      }
+    }
+    nc += zabs2(v);
+    if (le2 >= 1) nd += zabs2(zsub(v, v2));
+    if (kp > 0 && cprev) {
+      const double2 pv = m < kp ? cprev[(size_t)prob * ldp + m + 1] : make_double2(0.0, 0.0);
+      no += zabs2(zsub(v, pv));
+    }
+  }
+  nc = block_sum(nc, red);
+  nd = block_sum(nd, red);
+  no = block_sum(no, red);
+  if (tid == 0) {
+    const double cn = sqrt(nc);
+    // inner estimate: 0 when the inner space is exact (exhausted or l_eff = k)
+    double ei;
+    if (bad) ei = INFINITY;
+    else if (exact) ei = 0.0;
+    else if (le2 < 1 || w.rh_ok[count + prob] == 0) ei = INFINITY;
+    else ei = sqrt(nd) / cn;
+    est_inner[prob] = ei;
+    if (est_outer) est_outer[prob] = (kp > 0 && cprev && !bad) ? sqrt(no) / cn : INFINITY;
+    rh_status[prob] = bad ? (fail[prob] ? 2 : 1) : 0;
+    rh_iters[prob] = w.rh_its[prob];
+  }
+}
+
+static size_t inner_smem(int k) { return (size_t)13 * k * sizeof(double2) + 32 * sizeof(double) + k + 16; }
+
+cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermitian, const double2* alp,
+                      const double2* bet, const double2* gam, int ldc, InnerWork& w, double rh_tol, int rh_maxit,
+                      int inner_dl, double2* c, int ldo, void* cacc, int prec, double* est_inner,
+                      const double2* cprev, int ldp, const int* kprev_dev, double* est_outer, int* rh_status,
+                      int* rh_iters, cudaStream_t st) {
+  const size_t sm = inner_smem(w.ld);
+  cudaError_t e = cudaFuncSetAttribute(k_inner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_inner<<<count, kInnerThreads, sm, st>>>(k_dev, l_dev, hermitian, alp, bet, gam, ldc, w);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t esz = hermitian ? sizeof(double) : sizeof(double2);
+  // matrix + column buffer (which also holds the 64-double reduction scratch)
+  const size_t rsm = (size_t)kMaxL * kMaxL * esz + std::max<size_t>(kMaxL * esz, 512);
+  if (hermitian) {
+    e = cudaFuncSetAttribute(k_rh<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    if (e != cudaSuccess) return e;
+    k_rh<false><<<2 * count, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit);
+  } else {
+    e = cudaFuncSetAttribute(k_rh<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    if (e != cudaSuccess) return e;
+    k_rh<true><<<2 * count, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_combine<<<count, kInnerThreads, 0, st>>>(count, k_dev, l_dev, w, inner_dl, c, ldo, cacc, prec, est_inner, cprev,
+                                             ldp, kprev_dev, est_outer, rh_status, rh_iters);
+  return cudaGetLastError();
+}
+
+cudaError_t run_rh_dense(int count, int m, const double2* T, double2* S, int* iters, int* ok, double rh_tol,
+                         int rh_maxit, InnerWork& w, cudaStream_t st) {
+  const size_t rsm = (size_t)m * m * sizeof(double2) + std::max<size_t>(m * sizeof(double2), 512);
+  cudaError_t e = cudaFuncSetAttribute(k_rh<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+  if (e != cudaSuccess) return e;
+  k_rh<true><<<count, 1024, rsm, st>>>(count, m, T, w, 0, rh_tol, rh_maxit);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int i = 0; i < count; ++i) {
+    e = cudaMemcpy2DAsync(S + (size_t)i * m * m, sizeof(double2) * m * m, w.S + (size_t)i * kMaxL * kMaxL,
+                          sizeof(double2) * m * m, sizeof(double2) * m * m, 1, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaMemcpyAsync(iters, w.rh_its, sizeof(int) * count, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(ok, w.rh_ok, sizeof(int) * count, cudaMemcpyDeviceToDevice, st);
+}
+
+}  // namespace ov

@@ -1,0 +1,119 @@
+// Internal declarations shared by the libov translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/ov.h"
+
+namespace ov {
+
+constexpr int kBlock = 128;       // threads per block of the site kernels
+constexpr int kMaxL = 120;        // largest inner dimension (Roberts-Higham fits one CTA's shared memory)
+constexpr int kMaxInnerK = 1024;  // largest outer dimension the inner level accepts (H_k factors in shared memory)
+
+// status codes kept on the device per right-hand side
+constexpr int kStOK = 0;
+constexpr int kStLucky = 1;      // Lanczos found an invariant subspace at step kbreak
+constexpr int kStBreakdown = 2;  // serious two-sided breakdown at step kbreak
+constexpr int kStZero = 3;       // the source is zero: y = 0
+
+// Device coefficient arrays, each [nrhs][ld] (index j = 1..k is the step).
+struct Coefs {
+  double2* alp;  // alpha_j (complex; imaginary part 0 for Lanczos)
+  double2* bet;  // beta_j  (recurrence coefficient of the w_{j-1} / v_{j-1} terms)
+  double2* gam;  // gamma_j
+  double* nv;    // v_j = tv_j / nv_j
+  double2* nw;   // w_j = tw_j / conj(nw_j)
+  int* status;   // [nrhs]
+  int* kbreak;   // [nrhs]
+  int ld;
+};
+
+// Modes of the stencil step kernel.
+enum StepMode { kModeLanczos = 0, kModeTwoSided = 1, kModeRegen = 2, kModeApply = 3 };
+
+struct Geometry {
+  int V, Lx, Ly, Lz, Lt;
+};
+
+// Arguments of one outer step (all vector pointers are internal-layout arrays
+// [rhs][12][V] of the precision's storage type; strides in elements per RHS).
+struct StepArgs {
+  Geometry g;
+  int nrhs;
+  const void* links;
+  double mass;       // m_w + 4
+  double emu, emui;  // e^{mu}, e^{-mu}
+  const void* tv;
+  const void* tw;
+  const void* vprev;
+  const void* wprev;
+  void* vcur;
+  void* wcur;
+  void* p;
+  void* r;
+  void* tnext;  // regeneration pass: next unnormalised vector
+  void* yacc;   // regeneration pass: y accumulator (accumulator type)
+  const void* cacc;  // regeneration pass: c_j in accumulator type, [nrhs][ld]
+  size_t s_tv, s_tw, s_vprev, s_wprev, s_vcur, s_wcur, s_p, s_r, s_tnext, s_yacc;
+  Coefs c;
+  int j;
+  int dagger;  // apply mode: 1 = A^dag
+  double breakdown_tol;
+  double* partials;     // [nrhs][nblk][4]
+  unsigned* counters;   // [nrhs]
+};
+
+// outer-level launchers (ov_outer.cu); prec = OV_PREC_*
+cudaError_t launch_pack(int prec, const Geometry& g, int nrhs, const double2* xcanon, void* xint,
+                        size_t s_xint, Coefs c, double* partials, unsigned* counters, int want_norm,
+                        cudaStream_t st);
+cudaError_t launch_unpack(int prec, const Geometry& g, int nrhs, const void* xint, size_t s_xint,
+                          double2* ycanon, cudaStream_t st);
+cudaError_t launch_step(int prec, int mode, const StepArgs& a, cudaStream_t st);
+cudaError_t launch_update(int prec, int mode, const StepArgs& a, cudaStream_t st);
+// y_r = scale_r * sum_{j<k_r} c[r][j+1] v_{r,j+1} (+ x_r and gamma5 if add_x); slots[j] is
+// the device address of basis slot j (v_{j+1} of all RHS, RHS stride s_rhs elements)
+cudaError_t launch_recombine(int prec, const Geometry& g, int nrhs, const void* const* slots, size_t s_rhs,
+                             const void* cacc, int ldc, const int* k_dev, const double* scale,
+                             const double2* xcanon, int add_x, double2* ycanon, cudaStream_t st);
+// y_r = scale_r * yacc_r (+ x_r, gamma5)
+cudaError_t launch_finish_acc(int prec, const Geometry& g, int nrhs, const void* yacc, size_t s_yacc,
+                              const double* scale, const double2* xcanon, int add_x, double2* ycanon,
+                              cudaStream_t st);
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+size_t vec_elem_bytes(int prec);  // bytes per complex vector element
+size_t acc_elem_bytes(int prec);  // bytes per complex accumulator element
+int num_site_blocks(const Geometry& g);
+
+// inner level (ov_inner.cu)
+struct InnerWork {
+  // per problem i (batch of count problems):
+  double2* Q;       // [count][ld][kMaxL]  (row-major k x l_eff, leading dim kMaxL)
+  double2* T;       // [count][kMaxL][3]  inner alpha, beta, gamma
+  int* leff;        // [count]
+  double2* S;       // [2*count][kMaxL*kMaxL] Roberts-Higham scratch (global copy of S_n)
+  double2* s;       // [2*count][kMaxL]  first column of sgn(T)
+  int* rh_its;      // [2*count]
+  int* rh_ok;       // [2*count]
+  int* perm;        // [2*count][kMaxL]
+  int* fail;        // [count] singular H_k
+  int ld;
+};
+// Inner level for `count` problems whose tridiagonal coefficients live in device
+// arrays alp/bet/gam with leading dimension ldc (index j = 1..k as in Coefs, so the
+// diagonal is alp[j], the subdiagonal H_{j,j-1} = bet[j] and the superdiagonal
+// H_{j-1,j} = gam[j] for j >= 2). Results, index 1..k: c (double2 [count][ldo]) and, if
+// cacc is not NULL, c in the accumulator type of `prec`; est_inner[i]; est_outer[i]
+// against cprev (rows of length kprev[i], NULL: infinite); rh_status[i] (0 ok, 1 RH not
+// converged, 2 singular H); rh_iters[i].
+cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermitian, const double2* alp,
+                      const double2* bet, const double2* gam, int ldc, InnerWork& w, double rh_tol,
+                      int rh_maxit, int inner_dl, double2* c, int ldo, void* cacc, int prec,
+                      double* est_inner, const double2* cprev, int ldp, const int* kprev_dev,
+                      double* est_outer, int* rh_status, int* rh_iters, cudaStream_t st);
+cudaError_t run_rh_dense(int count, int m, const double2* T, double2* S, int* iters, int* ok,
+                         double rh_tol, int rh_maxit, InnerWork& w, cudaStream_t st);
+
+}  // namespace ov

@@ -1,0 +1,598 @@
+// Outer Krylov level: the gamma5 Wilson-Dirac stencil fused with the Lanczos /
+// two-sided Lanczos recurrences, vector updates with fixed-order reductions, and
+// recombination of the result (Sec. 2, Eq. (approximation); Sec. 3, Eq. (nested)).
+//
+// Layout: an internal spinor field is [rhs][12][V] of the precision's storage type
+// (component c = 3*spin + colour, site fastest), so a warp reads consecutive sites of
+// one component (coalesced). Links are [4][9][V] (nu, a*3+b, site) with the
+// antiperiodic t-boundary sign folded into U_t on the last time slice.
+//
+// Reductions: every block writes its partial sums (double) to a partials array; the
+// last block of each right-hand side (atomic ticket, no spin-wait) adds the partials in
+// a fixed order and writes the Krylov coefficient. Results are therefore bitwise
+// reproducible run to run.
+#include "ov_internal.h"
+#include "ov_types.cuh"
+
+namespace ov {
+
+int num_site_blocks(const Geometry& g) { return (g.V + kBlock - 1) / kBlock; }
+
+size_t vec_elem_bytes(int prec) {
+  return prec == OV_PREC_FP32 ? sizeof(float2) : (prec == OV_PREC_FP64 ? sizeof(double2) : sizeof(float4));
+}
+size_t acc_elem_bytes(int prec) { return prec == OV_PREC_FP64 ? sizeof(double2) : sizeof(float4); }
+
+template <class P> struct AccOf;
+template <> struct AccOf<PrecF64> { using A = double; using st = double2; };
+template <> struct AccOf<PrecF32> { using A = df64; using st = float4; };
+template <> struct AccOf<PrecDF64> { using A = df64; using st = float4; };
+
+__device__ __forceinline__ cx<double> ld_acc(const double2* p) { double2 v = *p; return {v.x, v.y}; }
+__device__ __forceinline__ cx<df64> ld_acc(const float4* p) { float4 v = *p; return {{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ void st_acc(double2* p, cx<double> a) { *p = make_double2(a.re, a.im); }
+__device__ __forceinline__ void st_acc(float4* p, cx<df64> a) { *p = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+
+// accumulator += c * v  (c in accumulator type, v in vector type)
+__device__ __forceinline__ void acc_axpy(cx<double>& y, cx<double> c, cx<double> v) { y = y + cmul(c, v); }
+__device__ __forceinline__ void acc_axpy(cx<df64>& y, cx<df64> c, cx<float> v) { y = y + lcmul<df64, float>(v, c); }
+__device__ __forceinline__ void acc_axpy(cx<df64>& y, cx<df64> c, cx<df64> v) { y = y + cmul(c, v); }
+
+__device__ __forceinline__ cx<double> acc_to_cd(cx<double> a) { return a; }
+__device__ __forceinline__ cx<double> acc_to_cd(cx<df64> a) { return {df_to_double(a.re), df_to_double(a.im)}; }
+__device__ __forceinline__ cx<double> vec_to_cd(cx<double> a) { return a; }
+__device__ __forceinline__ cx<double> vec_to_cd(cx<float> a) { return {(double)a.re, (double)a.im}; }
+__device__ __forceinline__ cx<double> vec_to_cd(cx<df64> a) { return {df_to_double(a.re), df_to_double(a.im)}; }
+
+template <class R> __device__ __forceinline__ cx<R> cd_to(double re, double im) {
+  return {from_double<R>(re), from_double<R>(im)};
+}
+
+// ------------------------------------------------------------ block reductions
+// Each thread passes its values; the block's sums go to partials[(r*nblk+bx)*4+q].
+// Returns true in the last block to finish for this right-hand side, where tot[]
+// (valid in thread 0) holds the fixed-order total over all blocks.
+template <int NQ>
+__device__ __forceinline__ bool reduce_last(double (&v)[NQ], double* partials, unsigned* counters, int r,
+                                            int nblk, double (&tot)[NQ]) {
+  __shared__ double sred[kBlock / 32][4];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double w = warp_sum(v[q]);
+    if (lane == 0) sred[warp][q] = w;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) s += sred[w][q];
+      partials[((size_t)r * nblk + blockIdx.x) * 4 + q] = s;
+    }
+    __threadfence();
+    unsigned prev = atomicAdd(&counters[r], 1u);
+    s_last = (prev == (unsigned)(nblk - 1));
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double loc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) loc[q] = 0.0;
+  for (int b = tid; b < nblk; b += kBlock) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) loc[q] += __ldcg(&partials[((size_t)r * nblk + b) * 4 + q]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double w = warp_sum(loc[q]);
+    if (lane == 0) sred[warp][q] = w;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) s += sred[w][q];
+      tot[q] = s;
+    }
+    counters[r] = 0u;
+  }
+  return true;
+}
+
+// warp sum in the accumulator type (double-float sums stay on the float pipes; double
+// arithmetic is used only once per warp); the result is valid in every lane
+__device__ __forceinline__ double warp_acc(double a) { return warp_sum(a); }
+__device__ __forceinline__ double warp_acc(df64 a) { return df_to_double(warp_sum(a)); }
+
+// ------------------------------------------------------------ pack / unpack
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_pack(Geometry g, const double2* __restrict__ x, typename P::vec_t* xi,
+                                                 size_t s_xi, Coefs c, double* partials, unsigned* counters,
+                                                 int want_norm) {
+  using R = typename P::R;
+  const int s = blockIdx.x * kBlock + threadIdx.x;
+  const int r = blockIdx.y;
+  double n2 = 0.0;
+  if (s < g.V) {
+    const double2* src = x + ((size_t)r * g.V + s) * 12;
+    typename P::vec_t* dst = xi + (size_t)r * s_xi + s;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 z = src[k];
+      n2 = fma(z.x, z.x, fma(z.y, z.y, n2));
+      st_vec(dst + (size_t)k * g.V, cd_to<R>(z.x, z.y));
+    }
+  }
+  if (!want_norm) return;
+  double v[1] = {n2}, tot[1];
+  if (reduce_last<1>(v, partials, counters, r, gridDim.x, tot) && threadIdx.x == 0) {
+    double nrm = sqrt(tot[0]);
+    size_t o = (size_t)r * c.ld + 1;
+    c.nv[o] = nrm > 0.0 ? nrm : 1.0;
+    c.nw[o] = make_double2(nrm > 0.0 ? nrm : 1.0, 0.0);
+    c.bet[o] = make_double2(0.0, 0.0);
+    c.gam[o] = make_double2(0.0, 0.0);
+    c.status[r] = nrm > 0.0 ? kStOK : kStZero;
+    c.kbreak[r] = 0;
+  }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_unpack(Geometry g, const typename P::vec_t* __restrict__ xi, size_t s_xi,
+                                                   double2* y) {
+  const int s = blockIdx.x * kBlock + threadIdx.x;
+  const int r = blockIdx.y;
+  if (s >= g.V) return;
+  const typename P::vec_t* src = xi + (size_t)r * s_xi + s;
+  double2* dst = y + ((size_t)r * g.V + s) * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    cx<double> z = vec_to_cd(ld_vec(src + (size_t)k * g.V));
+    dst[k] = make_double2(z.re, z.im);
+  }
+}
+
+// ------------------------------------------------------------ the stencil
+// Spin structure in the DeGrand-Rossi basis: gamma_nu = [[0, B],[B^dag, 0]] in 2x2 spin
+// blocks with B_x = [[0,i],[i,0]], B_y = [[0,-1],[1,0]], B_z = [[i,0],[0,-i]], B_t = 1.
+// Forward hop (1 - gamma): h = psi_u - B psi_l, result (U h, -B^dag U h).
+// Backward hop (1 + gamma): h = psi_u + B psi_l, result (U^dag h, +B^dag U^dag h).
+template <int NU, class R> __device__ __forceinline__ void bmul(cx<R> l0, cx<R> l1, cx<R>& b0, cx<R>& b1) {
+  if (NU == 0) { b0 = ci(l1); b1 = ci(l0); }
+  if (NU == 1) { b0 = -l1; b1 = l0; }
+  if (NU == 2) { b0 = ci(l0); b1 = cmi(l1); }
+  if (NU == 3) { b0 = l0; b1 = l1; }
+}
+template <int NU, class R> __device__ __forceinline__ void bdagmul(cx<R> g0, cx<R> g1, cx<R>& d0, cx<R>& d1) {
+  if (NU == 0) { d0 = cmi(g1); d1 = cmi(g0); }
+  if (NU == 1) { d0 = g1; d1 = -g0; }
+  if (NU == 2) { d0 = cmi(g0); d1 = ci(g1); }
+  if (NU == 3) { d0 = g0; d1 = g1; }
+}
+
+template <class P, int NU, bool FWD>
+__device__ __forceinline__ void hop(cx<typename P::R> (&acc)[12], const typename P::vec_t* __restrict__ src, int sn,
+                                    int V, const cx<typename P::L> (&u)[9], bool scale, typename P::R fac) {
+  using R = typename P::R;
+  using L = typename P::L;
+  cx<R> h0[3], h1[3];
+#pragma unroll
+  for (int col = 0; col < 3; ++col) {
+    cx<R> p0 = ld_vec(src + (size_t)(0 + col) * V + sn);
+    cx<R> p1 = ld_vec(src + (size_t)(3 + col) * V + sn);
+    cx<R> p2 = ld_vec(src + (size_t)(6 + col) * V + sn);
+    cx<R> p3 = ld_vec(src + (size_t)(9 + col) * V + sn);
+    cx<R> b0, b1;
+    bmul<NU>(p2, p3, b0, b1);
+    if (FWD) { h0[col] = p0 - b0; h1[col] = p1 - b1; }
+    else { h0[col] = p0 + b0; h1[col] = p1 + b1; }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cx<R> g0, g1;
+    if (FWD) {
+      g0 = lcmul<R, L>(u[a * 3 + 0], h0[0]) + lcmul<R, L>(u[a * 3 + 1], h0[1]) + lcmul<R, L>(u[a * 3 + 2], h0[2]);
+      g1 = lcmul<R, L>(u[a * 3 + 0], h1[0]) + lcmul<R, L>(u[a * 3 + 1], h1[1]) + lcmul<R, L>(u[a * 3 + 2], h1[2]);
+    } else {
+      g0 = lcmulc<R, L>(u[0 * 3 + a], h0[0]) + lcmulc<R, L>(u[1 * 3 + a], h0[1]) + lcmulc<R, L>(u[2 * 3 + a], h0[2]);
+      g1 = lcmulc<R, L>(u[0 * 3 + a], h1[0]) + lcmulc<R, L>(u[1 * 3 + a], h1[1]) + lcmulc<R, L>(u[2 * 3 + a], h1[2]);
+    }
+    if (scale) { g0 = cscale(g0, fac); g1 = cscale(g1, fac); }
+    cx<R> d0, d1;
+    bdagmul<NU>(g0, g1, d0, d1);
+    acc[0 + a] = acc[0 + a] + g0;
+    acc[3 + a] = acc[3 + a] + g1;
+    if (FWD) { acc[6 + a] = acc[6 + a] - d0; acc[9 + a] = acc[9 + a] - d1; }
+    else { acc[6 + a] = acc[6 + a] + d0; acc[9 + a] = acc[9 + a] + d1; }
+  }
+}
+
+__device__ __forceinline__ void site_coords(const Geometry& g, int s, int& x, int& y, int& z, int& t) {
+  x = s % g.Lx;
+  int q = s / g.Lx;
+  y = q % g.Ly;
+  q /= g.Ly;
+  z = q % g.Lz;
+  t = q / g.Lz;
+}
+
+template <class P, int NU>
+__device__ __forceinline__ void load_link(cx<typename P::L> (&u)[9], const typename P::link_t* __restrict__ links,
+                                          int V, int site) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) u[e] = ld_link(links + (size_t)(NU * 9 + e) * V + site);
+}
+
+// hopping sum for one source vector: acc = sum_nu [fwd + bwd], with e^{+-mu} on t
+// (sign = +1 for A, -1 for A^dag).
+template <class P, int NU>
+__device__ __forceinline__ void dir_pair(cx<typename P::R> (&acc)[12], const typename P::vec_t* __restrict__ src,
+                                         const typename P::link_t* __restrict__ links, int V, int s, int sf, int sb,
+                                         typename P::R ef, typename P::R eb) {
+  cx<typename P::L> u[9];
+  load_link<P, NU>(u, links, V, s);
+  hop<P, NU, true>(acc, src, sf, V, u, NU == 3, ef);
+  load_link<P, NU>(u, links, V, sb);
+  hop<P, NU, false>(acc, src, sb, V, u, NU == 3, eb);
+}
+
+template <class P>
+__device__ __forceinline__ void neighbours(const Geometry& g, int s, int (&sf)[4], int (&sb)[4]) {
+  int x, y, z, t;
+  site_coords(g, s, x, y, z, t);
+  const int sx = 1, sy = g.Lx, sz = g.Lx * g.Ly, st = g.Lx * g.Ly * g.Lz;
+  sf[0] = s + (x == g.Lx - 1 ? -(g.Lx - 1) * sx : sx);
+  sb[0] = s + (x == 0 ? (g.Lx - 1) * sx : -sx);
+  sf[1] = s + (y == g.Ly - 1 ? -(g.Ly - 1) * sy : sy);
+  sb[1] = s + (y == 0 ? (g.Ly - 1) * sy : -sy);
+  sf[2] = s + (z == g.Lz - 1 ? -(g.Lz - 1) * sz : sz);
+  sb[2] = s + (z == 0 ? (g.Lz - 1) * sz : -sz);
+  sf[3] = s + (t == g.Lt - 1 ? -(g.Lt - 1) * st : st);
+  sb[3] = s + (t == 0 ? (g.Lt - 1) * st : -st);
+}
+
+template <class P>
+__device__ __forceinline__ void hopping(cx<typename P::R> (&acc)[12], const typename P::vec_t* __restrict__ src,
+                                        const typename P::link_t* __restrict__ links, int V, int s, const int (&sf)[4],
+                                        const int (&sb)[4], typename P::R ef, typename P::R eb) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = czero<typename P::R>();
+  dir_pair<P, 0>(acc, src, links, V, s, sf[0], sb[0], ef, eb);
+  dir_pair<P, 1>(acc, src, links, V, s, sf[1], sb[1], ef, eb);
+  dir_pair<P, 2>(acc, src, links, V, s, sf[2], sb[2], ef, eb);
+  dir_pair<P, 3>(acc, src, links, V, s, sf[3], sb[3], ef, eb);
+}
+
+// (gamma5 D psi)_k at the centre site from the hopping sum: mass*psi - hop/2, lower spins negated.
+template <class R>
+__device__ __forceinline__ cx<R> g5d(int k, cx<R> psi, cx<R> hk, R mass) {
+  cx<R> d = cscale(psi, mass) - chalf(hk);
+  return k >= 6 ? -d : d;
+}
+
+template <class P, int MODE>
+__global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
+  using R = typename P::R;
+  using V_t = typename P::vec_t;
+  using L_t = typename P::link_t;
+  using A = typename P::A;
+  using AT = typename AccOf<P>::A;
+  using AS = typename AccOf<P>::st;
+  const Geometry g = a.g;
+  const int s = blockIdx.x * kBlock + threadIdx.x;
+  const int r = blockIdx.y;
+  const bool active = s < g.V;
+  const int ss = active ? s : 0;
+  const L_t* links = (const L_t*)a.links;
+  const R mass = from_double<R>(a.mass);
+  const R emu = from_double<R>(a.emu), emui = from_double<R>(a.emui);
+  const size_t co = (size_t)r * a.c.ld + a.j;
+
+  int sf[4], sb[4];
+  neighbours<P>(g, ss, sf, sb);
+
+  cx<A> dot = {rzero<A>(), rzero<A>()};
+  cx<R> acc[12];
+  const V_t* tv = (const V_t*)a.tv + (size_t)r * a.s_tv;
+
+  if (MODE == kModeApply) {
+    if (active) {
+      hopping<P>(acc, tv, links, g.V, s, sf, sb, a.dagger ? emui : emu, a.dagger ? emu : emui);
+      V_t* out = (V_t*)a.p + (size_t)r * a.s_p + s;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) st_vec(out + (size_t)k * g.V, g5d(k, ld_vec(tv + (size_t)k * g.V + s), acc[k], mass));
+    }
+    return;
+  }
+
+  // v side: v_j = tv / nv_j ; p = A v_j - gam_j v_{j-1}
+  const double invn = 1.0 / a.c.nv[co];
+  const R rinv = from_double<R>(invn);
+  const double2 gj = a.c.gam[co];
+  const cx<R> gam_j = cd_to<R>(gj.x, gj.y);
+  if (active) {
+    hopping<P>(acc, tv, links, g.V, s, sf, sb, emu, emui);
+    const V_t* vp = (const V_t*)a.vprev + (size_t)r * a.s_vprev + s;
+    V_t* vc = (V_t*)a.vcur + (size_t)r * a.s_vcur + s;
+    if (MODE == kModeRegen) {
+      // all coefficients are known: fuse the update and the y accumulation
+      const double2 aj = a.c.alp[co];
+      const cx<R> alp_j = cd_to<R>(aj.x, aj.y);
+      const AS* cj = (const AS*)a.cacc + (size_t)r * a.c.ld + a.j;
+      const cx<AT> cjv = ld_acc(cj);
+      V_t* tn = (V_t*)a.tnext + (size_t)r * a.s_tnext + s;
+      AS* ya = (AS*)a.yacc + (size_t)r * a.s_yacc + s;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const cx<R> psi = ld_vec(tv + (size_t)k * g.V + s);
+        const cx<R> v = cscale(psi, rinv);
+        const cx<R> pk = cscale(g5d(k, psi, acc[k], mass), rinv) - cmul(gam_j, ld_vec(vp + (size_t)k * g.V));
+        st_vec(vc + (size_t)k * g.V, v);
+        st_vec(tn + (size_t)k * g.V, pk - cmul(alp_j, v));
+        cx<AT> y = ld_acc(ya + (size_t)k * g.V);
+        acc_axpy(y, cjv, v);
+        st_acc(ya + (size_t)k * g.V, y);
+      }
+      return;
+    }
+    V_t* pp = (V_t*)a.p + (size_t)r * a.s_p + s;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const cx<R> psi = ld_vec(tv + (size_t)k * g.V + s);
+      const cx<R> v = cscale(psi, rinv);
+      const cx<R> pk = cscale(g5d(k, psi, acc[k], mass), rinv) - cmul(gam_j, ld_vec(vp + (size_t)k * g.V));
+      st_vec(vc + (size_t)k * g.V, v);
+      st_vec(pp + (size_t)k * g.V, pk);
+      if (MODE == kModeLanczos) acc_dot(dot, v, pk);
+    }
+  }
+  if (MODE == kModeRegen) return;
+
+  if (MODE == kModeTwoSided) {
+    // w side: w_j = tw / conj(nw_j) ; r = A^dag w_j - conj(bet_j) w_{j-1} ; alpha = w_j^dag p
+    const double2 nwj = a.c.nw[co];
+    const double den = nwj.x * nwj.x + nwj.y * nwj.y;
+    const cx<R> winv = cd_to<R>(nwj.x / den, nwj.y / den);  // 1/conj(nw) = nw/|nw|^2
+    const double2 bj = a.c.bet[co];
+    const cx<R> cbet = cd_to<R>(bj.x, -bj.y);
+    if (active) {
+      const V_t* tw = (const V_t*)a.tw + (size_t)r * a.s_tw;
+      hopping<P>(acc, tw, links, g.V, s, sf, sb, emui, emu);
+      const V_t* wp = (const V_t*)a.wprev + (size_t)r * a.s_wprev + s;
+      V_t* wc = (V_t*)a.wcur + (size_t)r * a.s_wcur + s;
+      V_t* rr = (V_t*)a.r + (size_t)r * a.s_r + s;
+      const V_t* pp = (const V_t*)a.p + (size_t)r * a.s_p + s;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const cx<R> psi = ld_vec(tw + (size_t)k * g.V + s);
+        const cx<R> w = cmul(winv, psi);
+        const cx<R> rk = cmul(winv, g5d(k, psi, acc[k], mass)) - cmul(cbet, ld_vec(wp + (size_t)k * g.V));
+        st_vec(wc + (size_t)k * g.V, w);
+        st_vec(rr + (size_t)k * g.V, rk);
+        acc_dot(dot, w, ld_vec(pp + (size_t)k * g.V));
+      }
+    }
+  }
+  double v2[2] = {warp_acc(dot.re), warp_acc(dot.im)}, tot[2];
+  // warp_acc already reduced over the warp in the accumulator type; reduce_last sums
+  // again over lanes, so keep only lane 0's value.
+  if ((threadIdx.x & 31) != 0) { v2[0] = 0.0; v2[1] = 0.0; }
+  if (reduce_last<2>(v2, a.partials, a.counters, r, gridDim.x, tot) && threadIdx.x == 0) {
+    a.c.alp[co] = make_double2(tot[0], MODE == kModeLanczos ? 0.0 : tot[1]);
+  }
+}
+
+// ------------------------------------------------------------ vector update
+template <class P, int MODE>
+__global__ void __launch_bounds__(kBlock) k_update(StepArgs a) {
+  using R = typename P::R;
+  using V_t = typename P::vec_t;
+  using A = typename P::A;
+  const Geometry g = a.g;
+  const int s = blockIdx.x * kBlock + threadIdx.x;
+  const int r = blockIdx.y;
+  const size_t co = (size_t)r * a.c.ld + a.j;
+  const double2 aj = a.c.alp[co];
+  const cx<R> alp = cd_to<R>(aj.x, aj.y);
+  const cx<R> calp = cd_to<R>(aj.x, -aj.y);
+  cx<A> d = {rzero<A>(), rzero<A>()};
+  cx<A> nvv = {rzero<A>(), rzero<A>()}, nww = {rzero<A>(), rzero<A>()};
+  if (s < g.V) {
+    const V_t* pp = (const V_t*)a.p + (size_t)r * a.s_p + s;
+    const V_t* vc = (const V_t*)a.vcur + (size_t)r * a.s_vcur + s;
+    V_t* tv = (V_t*)a.tv + (size_t)r * a.s_tv + s;  // written: the stencil no longer reads it
+    if (MODE == kModeLanczos) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const cx<R> t = ld_vec(pp + (size_t)k * g.V) - cmul(alp, ld_vec(vc + (size_t)k * g.V));
+        st_vec(tv + (size_t)k * g.V, t);
+        acc_dot(nvv, t, t);
+      }
+    } else {
+      const V_t* rr = (const V_t*)a.r + (size_t)r * a.s_r + s;
+      const V_t* wc = (const V_t*)a.wcur + (size_t)r * a.s_wcur + s;
+      V_t* tw = (V_t*)a.tw + (size_t)r * a.s_tw + s;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const cx<R> t = ld_vec(pp + (size_t)k * g.V) - cmul(alp, ld_vec(vc + (size_t)k * g.V));
+        const cx<R> u = ld_vec(rr + (size_t)k * g.V) - cmul(calp, ld_vec(wc + (size_t)k * g.V));
+        st_vec(tv + (size_t)k * g.V, t);
+        st_vec(tw + (size_t)k * g.V, u);
+        acc_dot(d, u, t);
+        acc_dot(nvv, t, t);
+        acc_dot(nww, u, u);
+      }
+    }
+  }
+  const bool lane0 = (threadIdx.x & 31) == 0;
+  if (MODE == kModeLanczos) {
+    double v1[1] = {warp_acc(nvv.re)}, tot[1];
+    if (!lane0) v1[0] = 0.0;
+    if (reduce_last<1>(v1, a.partials, a.counters, r, gridDim.x, tot) && threadIdx.x == 0) {
+      const double b = sqrt(tot[0]);
+      const double bprev = fabs(a.c.bet[co].x);
+      const size_t cn = co + 1;
+      const bool broke = !(b > a.breakdown_tol * (fabs(aj.x) + bprev));
+      if (broke && a.c.status[r] == kStOK) {
+        a.c.status[r] = kStLucky;
+        a.c.kbreak[r] = a.j;
+      }
+      const bool dead = a.c.status[r] != kStOK;
+      a.c.nv[cn] = dead ? 1.0 : b;
+      a.c.nw[cn] = make_double2(dead ? 1.0 : b, 0.0);
+      a.c.bet[cn] = make_double2(dead ? 0.0 : b, 0.0);
+      a.c.gam[cn] = make_double2(dead ? 0.0 : b, 0.0);
+    }
+  } else {
+    double v4[4] = {warp_acc(d.re), warp_acc(d.im), warp_acc(nvv.re), warp_acc(nww.re)}, tot[4];
+    if (!lane0) { v4[0] = v4[1] = v4[2] = v4[3] = 0.0; }
+    if (reduce_last<4>(v4, a.partials, a.counters, r, gridDim.x, tot) && threadIdx.x == 0) {
+      const double dre = tot[0], dim = tot[1];
+      const double ad = sqrt(dre * dre + dim * dim);
+      const double b = sqrt(ad);
+      const size_t cn = co + 1;
+      const bool broke = !(ad > a.breakdown_tol * sqrt(tot[2]) * sqrt(tot[3])) || !(b > 0.0);
+      if (broke && a.c.status[r] == kStOK) {
+        a.c.status[r] = kStBreakdown;
+        a.c.kbreak[r] = a.j;
+      }
+      const bool dead = a.c.status[r] != kStOK;
+      a.c.nv[cn] = dead ? 1.0 : b;
+      a.c.nw[cn] = dead ? make_double2(1.0, 0.0) : make_double2(dre / b, dim / b);
+      a.c.bet[cn] = make_double2(dead ? 0.0 : b, 0.0);
+      a.c.gam[cn] = dead ? make_double2(0.0, 0.0) : make_double2(dre / b, dim / b);
+    }
+  }
+}
+
+// ------------------------------------------------------------ recombination
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_recombine(Geometry g, const void* const* __restrict__ slots, size_t s_rhs,
+                                                      const typename AccOf<P>::st* __restrict__ cacc, int ldc,
+                                                      const int* __restrict__ kr, const double* __restrict__ scale,
+                                                      const double2* __restrict__ x, int add_x, double2* y) {
+  using AT = typename AccOf<P>::A;
+  const int s = blockIdx.x * kBlock + threadIdx.x;
+  const int r = blockIdx.y;
+  if (s >= g.V) return;
+  cx<AT> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = czero<AT>();
+  const int k_r = kr[r];
+  const typename AccOf<P>::st* cr = cacc + (size_t)r * ldc;
+  for (int j = 0; j < k_r; ++j) {
+    const cx<AT> cj = ld_acc(cr + j + 1);
+    const typename P::vec_t* vj = (const typename P::vec_t*)slots[j] + (size_t)r * s_rhs + s;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc_axpy(acc[k], cj, ld_vec(vj + (size_t)k * g.V));
+  }
+  const double sc = scale[r];
+  double2* dst = y + ((size_t)r * g.V + s) * 12;
+  const double2* xs = x + ((size_t)r * g.V + s) * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    cx<double> z = acc_to_cd(acc[k]);
+    z.re *= sc;
+    z.im *= sc;
+    if (add_x) {
+      const double2 xv = xs[k];
+      if (k >= 6) { z.re = -z.re; z.im = -z.im; }
+      z.re += xv.x;
+      z.im += xv.y;
+    }
+    dst[k] = make_double2(z.re, z.im);
+  }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_finish_acc(Geometry g, const typename AccOf<P>::st* __restrict__ yacc,
+                                                       size_t s_yacc, const double* __restrict__ scale,
+                                                       const double2* __restrict__ x, int add_x, double2* y) {
+  const int s = blockIdx.x * kBlock + threadIdx.x;
+  const int r = blockIdx.y;
+  if (s >= g.V) return;
+  const double sc = scale[r];
+  double2* dst = y + ((size_t)r * g.V + s) * 12;
+  const double2* xs = x + ((size_t)r * g.V + s) * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    cx<double> z = acc_to_cd(ld_acc(yacc + (size_t)r * s_yacc + (size_t)k * g.V + s));
+    z.re *= sc;
+    z.im *= sc;
+    if (add_x) {
+      const double2 xv = xs[k];
+      if (k >= 6) { z.re = -z.re; z.im = -z.im; }
+      z.re += xv.x;
+      z.im += xv.y;
+    }
+    dst[k] = make_double2(z.re, z.im);
+  }
+}
+
+// ------------------------------------------------------------ launchers
+static dim3 site_grid(const Geometry& g, int nrhs) { return dim3(num_site_blocks(g), nrhs); }
+
+#define OV_DISPATCH(prec, CALL)                      \
+  switch (prec) {                                    \
+    case OV_PREC_FP64: { using P = PrecF64; CALL; break; }  \
+    case OV_PREC_FP32: { using P = PrecF32; CALL; break; }  \
+    default: { using P = PrecDF64; CALL; break; }           \
+  }
+
+cudaError_t launch_pack(int prec, const Geometry& g, int nrhs, const double2* x, void* xi, size_t s_xi, Coefs c,
+                        double* partials, unsigned* counters, int want_norm, cudaStream_t st) {
+  OV_DISPATCH(prec, (k_pack<P><<<site_grid(g, nrhs), kBlock, 0, st>>>(g, x, (typename P::vec_t*)xi, s_xi, c,
+                                                                      partials, counters, want_norm)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int prec, const Geometry& g, int nrhs, const void* xi, size_t s_xi, double2* y,
+                          cudaStream_t st) {
+  OV_DISPATCH(prec, (k_unpack<P><<<site_grid(g, nrhs), kBlock, 0, st>>>(g, (const typename P::vec_t*)xi, s_xi, y)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(int prec, int mode, const StepArgs& a, cudaStream_t st) {
+  dim3 grid = site_grid(a.g, a.nrhs);
+  switch (mode) {
+    case kModeLanczos: OV_DISPATCH(prec, (k_step<P, kModeLanczos><<<grid, kBlock, 0, st>>>(a))); break;
+    case kModeTwoSided: OV_DISPATCH(prec, (k_step<P, kModeTwoSided><<<grid, kBlock, 0, st>>>(a))); break;
+    case kModeRegen: OV_DISPATCH(prec, (k_step<P, kModeRegen><<<grid, kBlock, 0, st>>>(a))); break;
+    default: OV_DISPATCH(prec, (k_step<P, kModeApply><<<grid, kBlock, 0, st>>>(a))); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(int prec, int mode, const StepArgs& a, cudaStream_t st) {
+  dim3 grid = site_grid(a.g, a.nrhs);
+  if (mode == kModeLanczos) {
+    OV_DISPATCH(prec, (k_update<P, kModeLanczos><<<grid, kBlock, 0, st>>>(a)));
+  } else {
+    OV_DISPATCH(prec, (k_update<P, kModeTwoSided><<<grid, kBlock, 0, st>>>(a)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recombine(int prec, const Geometry& g, int nrhs, const void* const* slots, size_t s_rhs,
+                             const void* cacc, int ldc, const int* k_dev, const double* scale, const double2* x,
+                             int add_x, double2* y, cudaStream_t st) {
+  OV_DISPATCH(prec, (k_recombine<P><<<site_grid(g, nrhs), kBlock, 0, st>>>(
+                        g, slots, s_rhs, (const typename AccOf<P>::st*)cacc, ldc, k_dev, scale, x, add_x, y)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_acc(int prec, const Geometry& g, int nrhs, const void* yacc, size_t s_yacc,
+                              const double* scale, const double2* x, int add_x, double2* y, cudaStream_t st) {
+  OV_DISPATCH(prec, (k_finish_acc<P><<<site_grid(g, nrhs), kBlock, 0, st>>>(
+                        g, (const typename AccOf<P>::st*)yacc, s_yacc, scale, x, add_x, y)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) { return cudaMemsetAsync(p, 0, bytes, st); }
+
+}  // namespace ov

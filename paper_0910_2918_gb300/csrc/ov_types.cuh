@@ -1,0 +1,220 @@
+// Device number types for the nested Krylov sign function.
+//
+// Three arithmetic modes share one kernel source:
+//   PrecF64  - double vectors, double links, double arithmetic;
+//   PrecF32  - float vectors, float links, float stencil; reductions in double-float;
+//   PrecDF64 - vectors as unevaluated float pairs (hi + lo), float links, error-free
+//              float arithmetic. The pair arithmetic is built from the exact
+//              transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2), Fast2Sum (Dekker
+//              1971) and the FMA product error p = a*b, e = fma(a, b, -p) (exact in
+//              IEEE arithmetic). Rounded operations inside them use the __f*_rn
+//              intrinsics so the compiler never contracts them into FMAs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ov {
+
+// ----------------------------------------------------------------- double-float
+struct df64 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df64 df_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  df64 s = df_two_sum(a.hi, b.hi);
+  float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return df_fast_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+// pair times a single float (links are exact floats)
+__device__ __forceinline__ df64 operator*(df64 a, float u) {
+  float p = __fmul_rn(a.hi, u);
+  float e = __fmaf_rn(a.hi, u, -p);
+  e = __fmaf_rn(a.lo, u, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df64 df_half(df64 a) { return {a.hi * 0.5f, a.lo * 0.5f}; }  // exact
+__device__ __forceinline__ df64 df_from_double(double d) {
+  float hi = __double2float_rn(d);
+  float lo = __double2float_rn(d - (double)hi);
+  return {hi, lo};
+}
+__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+__host__ __device__ __forceinline__ df64 df_zero() { return {0.f, 0.f}; }
+
+// ----------------------------------------------------------------- scalar helpers
+__device__ __forceinline__ double to_double(double a) { return a; }
+__device__ __forceinline__ double to_double(float a) { return (double)a; }
+__device__ __forceinline__ double to_double(df64 a) { return df_to_double(a); }
+
+template <class R> __device__ __forceinline__ R from_double(double d);
+template <> __device__ __forceinline__ double from_double<double>(double d) { return d; }
+template <> __device__ __forceinline__ float from_double<float>(double d) { return (float)d; }
+template <> __device__ __forceinline__ df64 from_double<df64>(double d) { return df_from_double(d); }
+
+template <class R> __device__ __forceinline__ R rzero();
+template <> __device__ __forceinline__ double rzero<double>() { return 0.0; }
+template <> __device__ __forceinline__ float rzero<float>() { return 0.f; }
+template <> __device__ __forceinline__ df64 rzero<df64>() { return df_zero(); }
+
+__device__ __forceinline__ double rhalf(double a) { return 0.5 * a; }
+__device__ __forceinline__ float rhalf(float a) { return 0.5f * a; }
+__device__ __forceinline__ df64 rhalf(df64 a) { return df_half(a); }
+
+// vector element times link element
+__device__ __forceinline__ double lmul(double v, double u) { return v * u; }
+__device__ __forceinline__ float lmul(float v, float u) { return v * u; }
+__device__ __forceinline__ df64 lmul(df64 v, float u) { return v * u; }
+
+// ----------------------------------------------------------------- complex
+template <class R>
+struct cx {
+  R re, im;
+};
+
+template <class R> __device__ __forceinline__ cx<R> czero() { return {rzero<R>(), rzero<R>()}; }
+template <class R> __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R> __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R> __device__ __forceinline__ cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+// multiply by i and -i
+template <class R> __device__ __forceinline__ cx<R> ci(cx<R> a) { return {-a.im, a.re}; }
+template <class R> __device__ __forceinline__ cx<R> cmi(cx<R> a) { return {a.im, -a.re}; }
+template <class R> __device__ __forceinline__ cx<R> chalf(cx<R> a) { return {rhalf(a.re), rhalf(a.im)}; }
+template <class R> __device__ __forceinline__ cx<R> cscale(cx<R> a, R s) { return {a.re * s, a.im * s}; }
+// full complex product
+template <class R> __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// conj(a) * b
+template <class R> __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+// link (type L) times vector element (type R): u * v and conj(u) * v
+template <class R, class L> __device__ __forceinline__ cx<R> lcmul(cx<L> u, cx<R> v) {
+  return {lmul(v.re, u.re) - lmul(v.im, u.im), lmul(v.im, u.re) + lmul(v.re, u.im)};
+}
+template <class R, class L> __device__ __forceinline__ cx<R> lcmulc(cx<L> u, cx<R> v) {
+  return {lmul(v.re, u.re) + lmul(v.im, u.im), lmul(v.im, u.re) - lmul(v.re, u.im)};
+}
+
+// ----------------------------------------------------------------- precision policies
+// vec_t: storage of one complex vector element; link_t: storage of one complex link
+// element; R: arithmetic of the stencil; L: link arithmetic; A: per-thread accumulator of
+// dot products (converted to double at warp level).
+struct PrecF64 {
+  using R = double;
+  using L = double;
+  using A = double;
+  using vec_t = double2;
+  using link_t = double2;
+  static constexpr int id = 0;
+};
+struct PrecF32 {
+  using R = float;
+  using L = float;
+  using A = df64;
+  using vec_t = float2;
+  using link_t = float2;
+  static constexpr int id = 1;
+};
+struct PrecDF64 {
+  using R = df64;
+  using L = float;
+  using A = df64;
+  using vec_t = float4;  // (re.hi, re.lo, im.hi, im.lo)
+  using link_t = float2;
+  static constexpr int id = 2;
+};
+
+__device__ __forceinline__ cx<double> ld_vec(const double2* p) {
+  double2 v = *p;
+  return {v.x, v.y};
+}
+__device__ __forceinline__ cx<float> ld_vec(const float2* p) {
+  float2 v = *p;
+  return {v.x, v.y};
+}
+__device__ __forceinline__ cx<df64> ld_vec(const float4* p) {
+  float4 v = *p;
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ void st_vec(double2* p, cx<double> a) { *p = make_double2(a.re, a.im); }
+__device__ __forceinline__ void st_vec(float2* p, cx<float> a) { *p = make_float2(a.re, a.im); }
+__device__ __forceinline__ void st_vec(float4* p, cx<df64> a) {
+  *p = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo);
+}
+__device__ __forceinline__ cx<double> ld_link(const double2* p) {
+  double2 v = __ldg(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ cx<float> ld_link(const float2* p) {
+  float2 v = __ldg(p);
+  return {v.x, v.y};
+}
+
+// accumulate conj(a) * b into a dot-product accumulator of type A
+__device__ __forceinline__ void acc_dot(cx<double>& acc, cx<double> a, cx<double> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+__device__ __forceinline__ df64 df_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ void acc_dot(cx<df64>& acc, cx<float> a, cx<float> b) {
+  acc.re = acc.re + df_prod(a.re, b.re);
+  acc.re = acc.re + df_prod(a.im, b.im);
+  acc.im = acc.im + df_prod(a.re, b.im);
+  acc.im = acc.im + df_prod(-a.im, b.re);
+}
+__device__ __forceinline__ void acc_dot(cx<df64>& acc, cx<df64> a, cx<df64> b) {
+  acc.re = acc.re + a.re * b.re;
+  acc.re = acc.re + a.im * b.im;
+  acc.im = acc.im + a.re * b.im;
+  acc.im = acc.im + (-a.im) * b.re;
+}
+__device__ __forceinline__ cx<double> acc_to_double(cx<double> a) { return a; }
+__device__ __forceinline__ cx<double> acc_to_double(cx<df64> a) {
+  return {df_to_double(a.re), df_to_double(a.im)};
+}
+
+// warp-level sum of a double-float (pairs travel through two shuffles)
+__device__ __forceinline__ df64 warp_sum(df64 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    df64 w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = v + w;
+  }
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace ov
