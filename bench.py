@@ -305,6 +305,23 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+def run_profile(args):
+    """One apply of the bench workload with k fixed to args.profile_steps (small
+    enough for an ncu capture: a few GB on the device)."""
+    import torch
+
+    import paper_0910_2918_gb300 as ov
+
+    U, X = make_inputs()
+    opts = ov.make_opts(k_fixed=args.profile_steps, recombination=0)
+    with ov.Overlap(DIMS, U, M_W, MU, PREC, opts=opts) as op:
+        xd = torch.from_numpy(X).cuda()
+        yd = torch.zeros_like(xd)
+        rc, info = op.sign_apply(xd, yd, TOL, K_MAX, min(L_INNER, args.profile_steps))
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_steps": args.profile_steps, "status": rc, "stats": op.stats()}), flush=True)
+
+
 def run_reference(args, rank, world):
     """The oracle as it stands, on the host cores, on the same workload and metric."""
     if rank != 0:
@@ -349,11 +366,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-validate", action="store_true", help="skip the FP64-path accuracy check")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="profiling run: one batched apply of the bench workload with exactly this many "
+                         "outer steps (no timing, baseline or validation); for ncu captures")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.profile_steps > 0:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)
