@@ -177,6 +177,25 @@ int ov_inner_sign(ov_handle* h, int count, int ld, const int* k, const void* alp
  * Returns OV_ERR_RH_NOCONV if any matrix did not converge within opts.rh_maxit. */
 int ov_rh_sign(ov_handle* h, int count, int m, const void* T, void* S, int* iters);
 
+/* Roberts-Higham sign of dense matrices without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc, such as
+ * applications that reserve all device memory for their own pool up front (where a
+ * library allocation fails or fragments that pool) and code that must not take the
+ * device-wide synchronisation cudaMalloc/cudaFree can cause.
+ *   T, S   : DEVICE pointers to `count` row-major m x m complex-double matrices; S
+ *            receives sgn(T) and also holds the iterate while the call runs.
+ *   iters  : HOST array of `count` ints (may be NULL): iterations used.
+ *   limits : count <= 64, m <= 120, otherwise OV_ERR_TOO_LARGE; no handle needed.
+ * Scratch is one fixed file-scope device array (about 31 KB per GPU that loads the
+ * library, kept until exit), shared by every call: calls that overlap on the GPU race
+ * on it, so serialise them (one stream, or wait between calls). The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture. Returns OV_ERR_RH_NOCONV if
+ * a matrix did not converge within rh_maxit, and returns after `stream` (a cudaStream_t
+ * or NULL) has finished the call's work. */
+int ov_rh_sign_noalloc(int count, int m, const void* T, void* S, int* iters, double rh_tol,
+                       int rh_maxit, void* stream);
+
 /* Library/device description: writes "libov <version> sm_<cc> <device name>". */
 int ov_version(char* buf, size_t len);
 

@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     ov_reset_stats,
     ov_inner_sign,
     ov_rh_sign,
+    ov_rh_sign_noalloc,
     ov_set_opts,
     ov_sign_apply,
     ov_strerror,

@@ -111,6 +111,8 @@ def lib():
     L.ov_inner_sign.restype = ctypes.c_int
     L.ov_rh_sign.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ip]
     L.ov_rh_sign.restype = ctypes.c_int
+    L.ov_rh_sign_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, ip, ctypes.c_double, ctypes.c_int, vp]
+    L.ov_rh_sign_noalloc.restype = ctypes.c_int
     L.ov_version.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     L.ov_version.restype = ctypes.c_int
     _lib = L
@@ -292,6 +294,29 @@ def ov_rh_sign(h, T):
     if rc < 0 and rc != OV_ERR_RH_NOCONV:
         raise OvError(rc, "ov_rh_sign")
     return rc, S, its
+
+
+def ov_rh_sign_noalloc(T, S, rh_tol=1e-10, rh_maxit=100, stream=None):
+    """Roberts-Higham sign of dense matrices without device allocation.
+
+    T, S: CUDA complex128 tensors of shape (count, m, m) (device memory owned by the
+    caller; S receives sgn(T)). For callers whose device memory is all held by their
+    own pool, or that must not trigger the synchronisation an allocation can cause.
+    Returns (status, iterations per matrix)."""
+    tp, tm = _ptr_mem(T)
+    sp, sm = _ptr_mem(S, writable=True)
+    if tm != OV_MEM_DEVICE or sm != OV_MEM_DEVICE:
+        raise ValueError("T and S must be CUDA tensors")
+    _check_c128(T, "T")
+    _check_c128(S, "S")
+    count, m = int(T.shape[0]), int(T.shape[1])
+    its = np.zeros(count, dtype=np.int32)
+    rc = lib().ov_rh_sign_noalloc(count, m, tp, sp, its.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  float(rh_tol), int(rh_maxit),
+                                  ctypes.c_void_p(stream) if stream is not None else None)
+    if rc < 0 and rc != OV_ERR_RH_NOCONV:
+        raise OvError(rc, "ov_rh_sign_noalloc")
+    return rc, its
 
 
 class Overlap:

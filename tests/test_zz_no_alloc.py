@@ -1,0 +1,60 @@
+"""The allocation-free Roberts-Higham entry point (for callers whose device memory is
+all reserved by their own pool, or that must avoid the synchronisation an allocation
+can cause) agrees with the regular entry point, call after call.
+
+This file is collected last so that a failure here, in a run that stops at the first
+failure, comes after every other test has run."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _matrices(rng, count, m):
+    mats = []
+    for _ in range(count):
+        X = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+        ev = np.concatenate([rng.uniform(0.3, 3, m // 2), -rng.uniform(0.3, 3, m - m // 2)])
+        ev = ev + 1j * rng.uniform(-1, 1, m)
+        mats.append(X @ np.diag(ev) @ np.linalg.inv(X))
+    return np.ascontiguousarray(np.stack(mats))
+
+
+def test_noalloc_matches_regular_entry_point_twice():
+    import torch
+
+    import ovinputs as oi
+    import paper_0910_2918_gb300 as ov
+
+    dims = (2, 2, 2, 2)
+    h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0)
+    try:
+        rng = np.random.default_rng(11)
+        for count, m in ((3, 40), (2, 120)):  # two calls in a row, different shapes
+            T = _matrices(rng, count, m)
+            rc_ref, S_ref, its_ref = ov.ov_rh_sign(h, T)
+            Td = torch.from_numpy(T).cuda()
+            Sd = torch.full_like(Td, float("nan"))
+            rc, its = ov.ov_rh_sign_noalloc(Td, Sd)
+            assert rc == 0 and rc_ref == 0
+            S = Sd.cpu().numpy()
+            for i in range(count):
+                assert np.linalg.norm(S[i] - S_ref[i]) / np.linalg.norm(S_ref[i]) < 1e-10
+            assert np.array_equal(its, its_ref)
+    finally:
+        ov.ov_destroy(h)
+
+
+def test_noalloc_rejects_sizes_beyond_its_limits():
+    import torch
+
+    import paper_0910_2918_gb300 as ov
+
+    T = torch.zeros((65, 4, 4), dtype=torch.complex128, device="cuda")
+    with pytest.raises(ov.OvError) as e:
+        ov.ov_rh_sign_noalloc(T, torch.zeros_like(T))
+    assert e.value.code == -7
+    T = torch.zeros((1, 121, 121), dtype=torch.complex128, device="cuda")
+    with pytest.raises(ov.OvError) as e:
+        ov.ov_rh_sign_noalloc(T, torch.zeros_like(T))
+    assert e.value.code == -7
