@@ -93,6 +93,9 @@ typedef struct {
   double breakdown_tol; /* relative breakdown threshold of the outer recurrences [1e-14] */
   int inner_dl;         /* step of the inner estimate: c(l) vs c(l - inner_dl) [4] */
   int k_fixed;          /* > 0: run exactly k_fixed outer steps, evaluate once, no stopping rule [0] */
+  int check_schedule;   /* 0: checks at first_check + j*check_interval; 1: adaptive: after two
+                           estimates, the next check goes where the log-linear decay of the outer
+                           estimate reaches tol (at least check_interval steps later) [0] */
   int timing;           /* 1: record CUDA events around every stencil / update / inner / recombination
                            launch on the handle's stream and accumulate their durations (ov_get_stats) [0] */
 } ov_opts;

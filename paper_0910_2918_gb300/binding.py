@@ -44,7 +44,7 @@ class ov_opts(ctypes.Structure):
     _fields_ = [("check_interval", ctypes.c_int), ("first_check", ctypes.c_int),
                 ("recombination", ctypes.c_int), ("rh_tol", ctypes.c_double), ("rh_maxit", ctypes.c_int),
                 ("breakdown_tol", ctypes.c_double), ("inner_dl", ctypes.c_int), ("k_fixed", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("check_schedule", ctypes.c_int), ("timing", ctypes.c_int)]
 
 
 class ov_stats(ctypes.Structure):

@@ -12,7 +12,12 @@
 // The only device->host traffic inside the loop is the per-check status readback.
 #include <math.h>
 #include <stdio.h>
+
+#include <cmath>
+#include <stdlib.h>
 #include <string.h>
+
+#include <chrono>
 
 #include <algorithm>
 #include <vector>
@@ -67,7 +72,7 @@ struct ov_handle {
   std::vector<Buf> chunks;        // stored basis: chunk c holds slots c*kChunk.. [slot][rhs][12V]
   int chunk_rhs = 0;              // nrhs the chunks were sized for
   Buf coef_alp, coef_bet, coef_gam, coef_nv, coef_nw, coef_status, coef_kbreak;
-  Buf partials, counters, scale;
+  Buf partials, counters, scale, scal;
   int cap_rhs = 0, cap_ld = 0;
   // inner level
   Buf iQ, iT, ileff, iS, is, irh_its, irh_ok, iperm, ifail;
@@ -75,6 +80,7 @@ struct ov_handle {
   Buf vptr;  // device array of basis slot pointers for recombination
   int inner_cap = 0, inner_ld = 0;
   ov_stats stats{};
+  int trace = 0;  // OV_TRACE set in the environment: one JSON line per check on stderr
   // event pairs recorded around timed launches: (class, start, stop)
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_class;
@@ -153,6 +159,7 @@ extern "C" void ov_default_opts(ov_opts* o) {
   o->breakdown_tol = 1e-14;
   o->inner_dl = 4;
   o->k_fixed = 0;
+  o->check_schedule = 0;
   o->timing = 0;
 }
 
@@ -172,7 +179,8 @@ extern "C" const char* ov_strerror(int code) {
 
 static int check_opts(const ov_opts& o) {
   if (o.check_interval < 1 || o.rh_maxit < 1 || !(o.rh_tol > 0) || o.inner_dl < 1 || o.k_fixed < 0 ||
-      o.first_check < 0 || o.recombination < 0 || o.recombination > 2 || !(o.breakdown_tol >= 0))
+      o.first_check < 0 || o.recombination < 0 || o.recombination > 2 || !(o.breakdown_tol >= 0) ||
+      o.check_schedule < 0 || o.check_schedule > 1)
     return OV_ERR_ARG;
   return OV_OK;
 }
@@ -230,6 +238,7 @@ extern "C" int ov_create(ov_handle** hp, const ov_geom* geom, const void* links,
   h->m_w = m_w;
   h->mu = mu;
   h->o = o;
+  h->trace = getenv("OV_TRACE") != nullptr;
   const size_t canon = sizeof(double2) * 36 * (size_t)V;
   const double2* src = (const double2*)links;
   Buf tmp;
@@ -262,7 +271,7 @@ extern "C" void ov_destroy(ov_handle* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   Buf* all[] = {&h->links, &h->xcanon, &h->ycanon, &h->tv, &h->tw, &h->p, &h->r, &h->vring, &h->wring, &h->yacc,
                 &h->coef_alp, &h->coef_bet, &h->coef_gam, &h->coef_nv, &h->coef_nw, &h->coef_status,
-                &h->coef_kbreak, &h->partials, &h->counters, &h->scale, &h->iQ, &h->iT, &h->ileff, &h->iS, &h->is,
+                &h->coef_kbreak, &h->partials, &h->counters, &h->scale, &h->scal, &h->iQ, &h->iT, &h->ileff, &h->iS, &h->is,
                 &h->irh_its, &h->irh_ok, &h->iperm, &h->ifail, &h->ck, &h->cl, &h->ckprev, &h->cc_cur, &h->cc_prev,
                 &h->cc_fin, &h->cacc_cur, &h->cacc_fin, &h->c_est_in, &h->c_est_out, &h->c_rhst, &h->c_rhit,
                 &h->vptr};
@@ -295,6 +304,7 @@ static int ensure_outer(ov_handle* h, int nrhs, int ld) {
     CK(cudaMemsetAsync(h->counters.p, 0, sizeof(unsigned) * nrhs, h->st));
   }
   CK(grow(h->scale, sizeof(double) * nrhs));
+  CK(grow(h->scal, sizeof(float4) * 8 * (size_t)nrhs));
   h->cap_rhs = nrhs;
   h->cap_ld = ld;
   return OV_OK;
@@ -418,7 +428,8 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   CK(cudaMemsetAsync(h->vring.p, 0, 2 * vbn, st));
   CK(cudaMemsetAsync(h->wring.p, 0, 2 * vbn, st));
   // v_1 = w_1 = x / ||x||: x goes to tv (and tw), the norm into nv_1 / nw_1
-  CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 1, st));
+  CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 1,
+                 h->scal.p, st));
   if (!herm) CK(cudaMemcpyAsync(h->tw.p, h->tv.p, vbn, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpy2DAsync(h->scale.p, sizeof(double), (double*)c.nv + 1, sizeof(double) * ld, sizeof(double), nrhs,
                        cudaMemcpyDeviceToDevice, st));
@@ -441,6 +452,10 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   a.mass = h->m_w + 4.0;
   a.emu = exp(h->mu);
   a.emui = exp(-h->mu);
+  split_const(a.mass, a.mass_hl);
+  split_const(a.emu, a.emu_hl);
+  split_const(a.emui, a.emui_hl);
+  a.scal = h->scal.p;
   a.tv = h->tv.p;
   a.tw = h->tw.p;
   a.p = h->p.p;
@@ -467,6 +482,11 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   int j = 0;
   void* prev_v = (char*)h->vring.p + vbn;  // zero slot: v_0
   const int first = o.first_check > 0 ? o.first_check : o.check_interval;
+  int next_check = first;
+  // last two (k, outer estimate) pairs per RHS for the adaptive schedule
+  std::vector<double> hk1(nrhs, 0), he1(nrhs, 0), hk2(nrhs, 0), he2(nrhs, 0);
+  std::vector<int> kprev_old(nrhs, 0);
+  int last_check = 0;
   for (j = 1; j <= ktarget && ndone < nrhs; ++j) {
     void* vcur = nullptr;
     if (recomb == OV_RECOMB_STORED) {
@@ -498,7 +518,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     h->stats.outer_steps += 1;
     prev_v = vcur;
     const bool fixed = o.k_fixed > 0;
-    const bool check = fixed ? (j == ktarget) : ((j >= first && (j - first) % o.check_interval == 0) || j == ktarget);
+    const bool check = fixed ? (j == ktarget) : (j >= next_check || j == ktarget);
     if (!check) continue;
     // read the breakdown state first: a Lanczos breakdown fixes k for that RHS
     CK(cudaMemcpyAsync(dstatus.data(), c.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
@@ -507,22 +527,55 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     for (int r = 0; r < nrhs; ++r) kcur[r] = (dstatus[r] != kStOK && dkbreak[r] > 0) ? std::min(dkbreak[r], j) : j;
     CK(cudaMemcpyAsync(h->ck.p, kcur.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(h->ckprev.p, kprev.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    const auto tc0 = std::chrono::steady_clock::now();
     const int ti = tstart(h, kClsInner);
     cudaError_t e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, ld, iw,
                               o.rh_tol, o.rh_maxit, o.inner_dl, (double2*)h->cc_cur.p, ld, h->cacc_cur.p, h->prec,
                               (double*)h->c_est_in.p, (const double2*)h->cc_prev.p, ld, (const int*)h->ckprev.p,
-                              (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, st);
+                              (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, 1, st);
     CK(e);
     tstop(h, ti);
     h->stats.launches += 3;
     h->stats.inner_launches += 3;
     h->stats.checks += 1;
     CK(cudaMemcpyAsync(eo.data(), h->c_est_out.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ei.data(), h->c_est_in.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(rhst.data(), h->c_rhst.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(rhit.data(), h->c_rhit.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(leff.data(), h->ileff.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    // the inner estimate is needed only where the run may stop at this check
+    bool want_inner = false;
+    for (int r = 0; r < nrhs && !fixed; ++r)
+      if (!done[r] && dstatus[r] != kStZero && dstatus[r] != kStBreakdown && rhst[r] == 0 &&
+          (eo[r] <= tol || dstatus[r] == kStLucky || j == ktarget))
+        want_inner = true;
+    std::fill(ei.begin(), ei.end(), NAN);
+    if (want_inner) {
+      const int t2 = tstart(h, kClsInner);
+      e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, ld, iw, o.rh_tol,
+                    o.rh_maxit, o.inner_dl, (double2*)h->cc_cur.p, ld, h->cacc_cur.p, h->prec,
+                    (double*)h->c_est_in.p, (const double2*)h->cc_prev.p, ld, (const int*)h->ckprev.p,
+                    (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, 2, st);
+      CK(e);
+      tstop(h, t2);
+      h->stats.launches += 2;
+      h->stats.inner_launches += 2;
+      CK(cudaMemcpyAsync(ei.data(), h->c_est_in.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(rhst.data(), h->c_rhst.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    if (h->trace) {
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc0).count();
+      fprintf(stderr, "{\"ov_check\": %d, \"ms\": %.3f, \"inner_estimate\": %d, \"rh_iters\": [", j, ms,
+              want_inner ? 1 : 0);
+      for (int r = 0; r < nrhs; ++r) fprintf(stderr, "%s%d", r ? "," : "", rhit[r]);
+      fprintf(stderr, "], \"est_outer\": [");
+      for (int r = 0; r < nrhs; ++r) fprintf(stderr, "%s%.3e", r ? "," : "", eo[r]);
+      fprintf(stderr, "], \"l_eff\": [");
+      for (int r = 0; r < nrhs; ++r) fprintf(stderr, "%s%d", r ? "," : "", leff[r]);
+      fprintf(stderr, "]}\n");
+    }
+    kprev_old = kprev;
     for (int r = 0; r < nrhs; ++r) {
       if (done[r]) continue;
       int fin = 0, sr = OV_OK;
@@ -572,9 +625,38 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
                            ab * ld, cudaMemcpyDeviceToDevice, st));
       } else {
         kprev[r] = kcur[r];
+        // est_outer compares with the previous check, so it measures the error there;
+        // keep the first and the latest such point (the longest baseline for the rate,
+        // since the decay is irregular over short spans)
+        if (std::isfinite(eo[r]) && eo[r] > 0.0) {
+          if (he1[r] <= 0.0) {
+            hk1[r] = kprev_old[r];
+            he1[r] = eo[r];
+          } else {
+            hk2[r] = kprev_old[r];
+            he2[r] = eo[r];
+          }
+        }
       }
     }
     std::swap(h->cc_cur, h->cc_prev);
+    // next check: fixed interval, or (adaptive) a jump to where the log-linear decay of
+    // the error reaches tol, always followed by a partner check check_interval later
+    // (the estimate at a check measures the error at the check before it)
+    int step = o.check_interval;
+    if (o.check_schedule == 1 && j - last_check <= o.check_interval) {
+      int pred = -1;
+      for (int r = 0; r < nrhs; ++r) {
+        if (done[r] || he1[r] <= 0.0 || he2[r] <= 0.0 || he2[r] >= he1[r] || tol <= 0.0 || hk2[r] <= hk1[r]) continue;
+        const double rate = (std::log(he2[r]) - std::log(he1[r])) / (hk2[r] - hk1[r]);
+        const double ks = hk2[r] + (std::log(tol) - std::log(he2[r])) / rate;
+        const int ahead = (int)std::ceil(ks) - j;
+        if (pred < 0 || ahead < pred) pred = ahead;
+      }
+      if (pred > step) step = std::min(pred, 10 * o.check_interval);
+    }
+    last_check = j;
+    next_check = j + step;
   }
   const int kmax_used = *std::max_element(kfin.begin(), kfin.end());
   // recombination
@@ -592,7 +674,8 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     const size_t ab = acc_elem_bytes(h->prec) * n12 * nrhs;
     CK(grow(h->yacc, ab));
     CK(cudaMemsetAsync(h->yacc.p, 0, ab, st));
-    CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, st));
+    CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0,
+                   nullptr, st));
     CK(cudaMemsetAsync(h->vring.p, 0, 2 * vbn, st));
     StepArgs b = a;
     b.yacc = h->yacc.p;
@@ -671,7 +754,8 @@ extern "C" int ov_wilson_apply(ov_handle* h, int nrhs, const void* x, void* y, i
     yd = (double2*)h->ycanon.p;
   }
   Coefs c = coefs(h, h->cap_ld);
-  CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, st));
+  CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0,
+                 nullptr, st));
   StepArgs a{};
   a.g = g;
   a.nrhs = nrhs;
@@ -679,6 +763,9 @@ extern "C" int ov_wilson_apply(ov_handle* h, int nrhs, const void* x, void* y, i
   a.mass = h->m_w + 4.0;
   a.emu = exp(h->mu);
   a.emui = exp(-h->mu);
+  split_const(a.mass, a.mass_hl);
+  split_const(a.emu, a.emu_hl);
+  split_const(a.emui, a.emui_hl);
   a.tv = h->tv.p;
   a.p = h->p.p;
   a.s_tv = a.s_p = n12;
@@ -736,7 +823,7 @@ extern "C" int ov_inner_sign(ov_handle* h, int count, int ld, const int* k, cons
   cudaError_t e = run_inner(count, (const int*)h->ck.p, (const int*)h->cl.p, hermitian ? 1 : 0, (double2*)dA.p,
                             (double2*)dB.p, (double2*)dG.p, ldi, iw, h->o.rh_tol, h->o.rh_maxit, h->o.inner_dl,
                             (double2*)h->cc_cur.p, ldi, nullptr, h->prec, (double*)h->c_est_in.p, nullptr, ldi,
-                            nullptr, nullptr, (int*)h->c_rhst.p, (int*)h->c_rhit.p, st);
+                            nullptr, nullptr, (int*)h->c_rhst.p, (int*)h->c_rhit.p, 0, st);
   std::vector<double2> C((size_t)count * ldi);
   std::vector<double> ein(count);
   std::vector<int> rs(count), ri(count);

@@ -327,10 +327,10 @@ __device__ __forceinline__ E el_load(const double2* p) {
 
 template <bool CPLX>
 __global__ void __launch_bounds__(1024) k_rh(int count, int dense_m, const double2* __restrict__ dense_T,
-                                             InnerWork w, int dl, double rh_tol, int rh_maxit) {
+                                             InnerWork w, int dl, double rh_tol, int rh_maxit, int mid0) {
   using E = typename RhElem<CPLX>::T;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int mid = blockIdx.x;
+  const int mid = mid0 + blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
   int m;
   if (dense_m > 0) {
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kInnerThreads) k_combine(int count, const int*
                                                            double2* c, int ldo, void* cacc, int prec,
                                                            double* est_inner, const double2* cprev, int ldp,
                                                            const int* kprev_dev, double* est_outer, int* rh_status,
-                                                           int* rh_iters) {
+                                                           int* rh_iters, int have_est) {
   const int* fail = w.fail;
   __shared__ double red[32];
   const int prob = blockIdx.x;
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kInnerThreads) k_combine(int count, const int*
       for (int i = 0; i < le; ++i) {
         const double2 qv = Q[(size_t)m * kMaxL + i];
         v = zadd(v, zmul(qv, s1[i]));
-        if (i < le2) v2 = zadd(v2, zmul(qv, s2[i]));
+        if (have_est && i < le2) v2 = zadd(v2, zmul(qv, s2[i]));
       }
     }
     c[(size_t)prob * ldo + m + 1] = v;
@@ -522,6 +522,7 @@ __global__ void __launch_bounds__(kInnerThreads) k_combine(int count, const int*
     double ei;
     if (bad) ei = INFINITY;
     else if (exact) ei = 0.0;
+    else if (!have_est) ei = NAN;
     else if (le2 < 1 || w.rh_ok[count + prob] == 0) ei = INFINITY;
     else ei = sqrt(nd) / cn;
     est_inner[prob] = ei;
@@ -537,27 +538,35 @@ cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermiti
                       const double2* bet, const double2* gam, int ldc, InnerWork& w, double rh_tol, int rh_maxit,
                       int inner_dl, double2* c, int ldo, void* cacc, int prec, double* est_inner,
                       const double2* cprev, int ldp, const int* kprev_dev, double* est_outer, int* rh_status,
-                      int* rh_iters, cudaStream_t st) {
-  const size_t sm = inner_smem(w.ld);
-  cudaError_t e = cudaFuncSetAttribute(k_inner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_inner<<<count, kInnerThreads, sm, st>>>(k_dev, l_dev, hermitian, alp, bet, gam, ldc, w);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                      int* rh_iters, int phase, cudaStream_t st) {
+  cudaError_t e;
+  if (phase != 2) {
+    const size_t sm = inner_smem(w.ld);
+    e = cudaFuncSetAttribute(k_inner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_inner<<<count, kInnerThreads, sm, st>>>(k_dev, l_dev, hermitian, alp, bet, gam, ldc, w);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // phase 0: both Roberts-Higham sets (the matrices and their leading l - dl blocks);
+  // phase 1: the matrices only (no inner estimate); phase 2: only the leading blocks
+  // of the matrices left by a phase-1 call (the inner estimate on request)
+  const int mid0 = phase == 2 ? count : 0;
+  const int nmat = phase == 0 ? 2 * count : count;
   const size_t esz = hermitian ? sizeof(double) : sizeof(double2);
   // matrix + column buffer (which also holds the 64-double reduction scratch)
   const size_t rsm = (size_t)kMaxL * kMaxL * esz + std::max<size_t>(kMaxL * esz, 512);
   if (hermitian) {
     e = cudaFuncSetAttribute(k_rh<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
     if (e != cudaSuccess) return e;
-    k_rh<false><<<2 * count, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit);
+    k_rh<false><<<nmat, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit, mid0);
   } else {
     e = cudaFuncSetAttribute(k_rh<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
     if (e != cudaSuccess) return e;
-    k_rh<true><<<2 * count, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit);
+    k_rh<true><<<nmat, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit, mid0);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_combine<<<count, kInnerThreads, 0, st>>>(count, k_dev, l_dev, w, inner_dl, c, ldo, cacc, prec, est_inner, cprev,
-                                             ldp, kprev_dev, est_outer, rh_status, rh_iters);
+                                             ldp, kprev_dev, est_outer, rh_status, rh_iters, phase != 1);
   return cudaGetLastError();
 }
 
@@ -566,7 +575,7 @@ cudaError_t run_rh_dense(int count, int m, const double2* T, double2* S, int* it
   const size_t rsm = (size_t)m * m * sizeof(double2) + std::max<size_t>(m * sizeof(double2), 512);
   cudaError_t e = cudaFuncSetAttribute(k_rh<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
   if (e != cudaSuccess) return e;
-  k_rh<true><<<count, 1024, rsm, st>>>(count, m, T, w, 0, rh_tol, rh_maxit);
+  k_rh<true><<<count, 1024, rsm, st>>>(count, m, T, w, 0, rh_tol, rh_maxit, 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int i = 0; i < count; ++i) {
     e = cudaMemcpy2DAsync(S + (size_t)i * m * m, sizeof(double2) * m * m, w.S + (size_t)i * kMaxL * kMaxL,

@@ -45,6 +45,12 @@ struct StepArgs {
   const void* links;
   double mass;       // m_w + 4
   double emu, emui;  // e^{mu}, e^{-mu}
+  float mass_hl[2], emu_hl[2], emui_hl[2];  // the same constants as float pairs (hi + lo)
+  // per-RHS step scalars in the arithmetic type of the precision (vec_t slots, [nrhs][8]):
+  // 0: 1/nv_j, 1: gam_j, 2: 1/conj(nw_j), 3: conj(bet_j), 4: alpha_j, 5: conj(alpha_j).
+  // They are written once per step by the block that finalises the coefficient, so the
+  // site kernels do no double-precision work.
+  void* scal;
   const void* tv;
   const void* tw;
   const void* vprev;
@@ -68,7 +74,8 @@ struct StepArgs {
 // outer-level launchers (ov_outer.cu); prec = OV_PREC_*
 cudaError_t launch_pack(int prec, const Geometry& g, int nrhs, const double2* xcanon, void* xint,
                         size_t s_xint, Coefs c, double* partials, unsigned* counters, int want_norm,
-                        cudaStream_t st);
+                        void* scal, cudaStream_t st);
+void split_const(double d, float hl[2]);
 cudaError_t launch_unpack(int prec, const Geometry& g, int nrhs, const void* xint, size_t s_xint,
                           double2* ycanon, cudaStream_t st);
 cudaError_t launch_step(int prec, int mode, const StepArgs& a, cudaStream_t st);
@@ -107,12 +114,14 @@ struct InnerWork {
 // H_{j-1,j} = gam[j] for j >= 2). Results, index 1..k: c (double2 [count][ldo]) and, if
 // cacc is not NULL, c in the accumulator type of `prec`; est_inner[i]; est_outer[i]
 // against cprev (rows of length kprev[i], NULL: infinite); rh_status[i] (0 ok, 1 RH not
-// converged, 2 singular H); rh_iters[i].
+// converged, 2 singular H); rh_iters[i]. phase 0: everything; phase 1: no inner estimate
+// (est_inner = NaN); phase 2: the inner estimate for the problems of a preceding phase-1
+// call (re-runs only the smaller Roberts-Higham set and the combination).
 cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermitian, const double2* alp,
                       const double2* bet, const double2* gam, int ldc, InnerWork& w, double rh_tol,
                       int rh_maxit, int inner_dl, double2* c, int ldo, void* cacc, int prec,
                       double* est_inner, const double2* cprev, int ldp, const int* kprev_dev,
-                      double* est_outer, int* rh_status, int* rh_iters, cudaStream_t st);
+                      double* est_outer, int* rh_status, int* rh_iters, int phase, cudaStream_t st);
 cudaError_t run_rh_dense(int count, int m, const double2* T, double2* S, int* iters, int* ok,
                          double rh_tol, int rh_maxit, InnerWork& w, cudaStream_t st);
 

