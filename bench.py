@@ -46,8 +46,8 @@ PROFILE = os.path.join(ROOT, "profiles", "stencil_twosided_df64_16x16x16x16_12rh
 def workload_desc():
     return (f"{DIMS[0]}^4 lattice, near-unit links eps={EPS} (seed 0), mu={MU}, m_w={M_W}, "
             f"{NRHS} spin-colour point sources at site 0, tol {TOL:g}, k<={K_MAX}, l={L_INNER}, "
-            f"checks from k={CHECK_FIRST} every >={CHECK_EVERY} steps (adaptive schedule), "
-            f"double-float vectors / float links")
+            f"first check at the learned k* (else k={CHECK_FIRST}), then every >={CHECK_EVERY} steps "
+            f"(adaptive schedule), l from the learned l* (<= {L_INNER}), double-float vectors / float links")
 
 
 def make_inputs():
@@ -189,6 +189,12 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     opts = ov.make_opts(check_interval=CHECK_EVERY, first_check=CHECK_FIRST, check_schedule=1, timing=1)
     op = ov.Overlap(DIMS, U, M_W, MU, PREC, opts=opts, stream=stream.cuda_stream)
+    # learned sizing: the committed network predicts the first check and l after 16 steps
+    sized = not args.no_sizer
+    if sized:
+        from paper_0910_2918_gb300 import sizer
+
+        op.set_sizer(sizer.load(sizer.DEFAULT_PARAMS), 8, L_INNER)
     xd = torch.from_numpy(X).cuda()
     yd = torch.zeros_like(xd)
     xh = torch.from_numpy(X).pin_memory()
@@ -236,6 +242,44 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(gsum, op=dist.ReduceOp.SUM)
     ms_max, e2e_ms = float(tmax[0]), float(tmax[1])
     good_all, good_e2e_all = float(gsum[0]), float(gsum[1])
+    # the float (mixed-precision) stencil on the same workload: HBM fraction of its fused
+    # two-sided step (k fixed, outside the timed region)
+    fp32_stencil = None
+    if rank == 0 and not args.no_fp32:
+        with ov.Overlap(DIMS, U, M_W, MU, "fp32", opts=ov.make_opts(k_fixed=60, timing=1),
+                        stream=stream.cuda_stream) as op32:
+            y32 = torch.zeros_like(xd)
+            op32.sign_apply(xd, y32, TOL, K_MAX, 8)
+            op32.reset_stats()
+            op32.sign_apply(xd, y32, TOL, K_MAX, 8)
+            s32 = op32.stats()
+        V = int(np.prod(DIMS))
+        b32 = V * (NRHS * 8 * 12 * 8 + 4 * 9 * 8)
+        t32 = s32["stencil_ms"] / max(s32["stencil_launches"], 1)
+        fp32_stencil = {"kernel": "k_step<PrecF32, two-sided>", "alg_bytes_per_launch": b32, "avg_launch_ms": t32,
+                        "achieved_gbs": b32 / (t32 * 1e-3) / 1e9,
+                        "frac_of_measured_hbm": b32 / (t32 * 1e-3) / 1e9 / (peaks() or {}).get("hbm_gbs", 6800.0),
+                        "block_size": s32["block_size"]}
+    # the plain FP64 nested method (FP64 vectors, one RHS at a time, checks every 10 steps,
+    # no sizing) on a sample of the same RHS: the speedup of the fast form at equal accuracy
+    plain = None
+    if rank == 0 and not args.no_plain:
+        sel = [0, 7]
+        t_plain, err_plain = 0.0, 0.0
+        with ov.Overlap(DIMS, U, M_W, MU, "fp64", opts=ov.make_opts(check_interval=10),
+                        stream=stream.cuda_stream) as opp:
+            yp = torch.zeros((1, n), dtype=torch.complex128, device="cuda")
+            opp.sign_apply(xd[0:1].contiguous(), yp, TOL, K_MAX, L_INNER)  # warm-up
+            for r in sel:
+                torch.cuda.synchronize()
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ea.record(stream)
+                opp.sign_apply(xd[r:r + 1].contiguous(), yp, TOL, K_MAX, L_INNER)
+                eb.record(stream)
+                torch.cuda.synchronize()
+                t_plain += ea.elapsed_time(eb)
+        plain = {"applies_per_s": len(sel) / (t_plain * 1e-3), "sample": f"RHS {sel} one at a time",
+                 "form": "FP64 vectors, one RHS per call, checks every 10 steps, l=%d, no sizing" % L_INNER}
     # accuracy against the double-precision path (outside the timed region, rank 0)
     err_fp64 = None
     if rank == 0 and not args.no_validate:
@@ -286,14 +330,19 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "df64",
         "data": "synthetic",
         "config": {"workload": workload_desc(), "global_batch": NRHS * world, "parallelism": f"replicas{world}",
+                   "learned_sizing": sized,
                    "l2": "working set per step >> L2 (12 x k x 12.6 MB stored basis)", "k_used": k_used,
                    "l_used": l_used, "applies_within_tol": good_frac, "rel_err_vs_fp64_path": err_fp64},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "kernel": "k_step<PrecDF64, two-sided> (fused A, A^dag stencil + recurrence)",
-                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": st_ms, "peak_source": peak_src},
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": st_ms, "peak_source": peak_src,
+                     "block_size": st["block_size"]},
         "phase_ms_per_step": {"stencil": st["stencil_ms"] / args.steps, "update": st["update_ms"] / args.steps,
                               "inner": st["inner_ms"] / args.steps, "recombine": st["recombine_ms"] / args.steps,
                               "checks": st["checks"] / args.steps},
+        "stencil_fp32": fp32_stencil,
+        "plain_fp64_nested": plain,
+        "speedup_vs_plain_fp64": (value * good_frac / plain["applies_per_s"]) if plain else None,
         "cpu_baseline": cpu,
         "e2e": {"value": world * NRHS * args.steps / (e2e_ms * 1e-3) * (good_e2e_all / (world * NRHS * args.steps)),
                 "unit": "applies/s", "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(X.nbytes)},
@@ -367,6 +416,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-validate", action="store_true", help="skip the FP64-path accuracy check")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the float-stencil measurement")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 nested-method comparison")
+    ap.add_argument("--no-sizer", action="store_true", help="run without the learned sizing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling run: one batched apply of the bench workload with exactly this many "

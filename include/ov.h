@@ -96,6 +96,9 @@ typedef struct {
   int check_schedule;   /* 0: checks at first_check + j*check_interval; 1: adaptive: after two
                            estimates, the next check goes where the log-linear decay of the outer
                            estimate reaches tol (at least check_interval steps later) [0] */
+  int block_size;       /* threads per block of the site kernels: 64, 128, 256, or 0 = autotune
+                           (time the first outer step at each size once per handle and problem
+                           set, keep the fastest) [0] */
   int timing;           /* 1: record CUDA events around every stencil / update / inner / recombination
                            launch on the handle's stream and accumulate their durations (ov_get_stats) [0] */
 } ov_opts;
@@ -113,6 +116,7 @@ typedef struct {
   long long outer_steps;       /* outer Krylov steps run (first pass) */
   long long regen_steps;       /* steps of the second (regeneration) pass */
   long long checks;            /* stopping checks (inner evaluations) */
+  long long block_size;        /* threads per site block of the last apply (autotuned or forced) */
 } ov_stats;
 
 /* Per-RHS result information. */
@@ -157,6 +161,21 @@ int ov_sign_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, doubl
 int ov_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max,
              int l, ov_info* info);
 
+/* A batch of independent lattice problems of uneven sizes (one source each), advanced
+ * together: every outer step is one launch over all problems' sites, and each check
+ * runs the inner level of all problems together. geoms[i], links[i], m_w[i], mu[i]
+ * describe problem i (all with the same precision and t boundary); the handle it
+ * writes is used with ov_batch_sign_apply (and ov_wilson_apply with nrhs = nprob, x/y
+ * then being the problems' spinors concatenated) and released with ov_destroy. When any
+ * mu[i] != 0 every problem runs two-sided Lanczos (at mu = 0 it equals Lanczos, Sec. 2). */
+int ov_batch_create(ov_handle** h, int nprob, const ov_geom* geoms, const void* const* links,
+                    int links_mem, const double* m_w, const double* mu, const ov_opts* opts,
+                    void* stream);
+/* y[i] = sgn(gamma5 D_w(mu_i)) x[i] for every problem i; x[i], y[i]: 12 V_i complex doubles
+ * (canonical layout; `mem` says where). info: nprob entries (may be NULL). */
+int ov_batch_sign_apply(ov_handle* h, const void* const* x, void* const* y, int mem, double tol,
+                        int k_max, int l, ov_info* info);
+
 /* y_r = A x_r with A = gamma5 D_w(mu) (dagger = 0) or A^dag = gamma5 D_w(-mu)
  * (dagger = 1): the stencil alone, in the handle's arithmetic (Sec. 1). */
 int ov_wilson_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, int dagger);
@@ -179,6 +198,41 @@ int ov_inner_sign(ov_handle* h, int count, int ld, const int* k, const void* alp
  * matrices (row-major complex doubles, HOST memory, m <= 120), written to S (host).
  * Returns OV_ERR_RH_NOCONV if any matrix did not converge within opts.rh_maxit. */
 int ov_rh_sign(ov_handle* h, int count, int m, const void* T, void* S, int* iters);
+
+/* ---- learned sizing of the Krylov dimensions (not in the paper) ----
+ * A 16 -> 64 -> 64 -> 2 float MLP with ReLU reads f = (Im alpha_1..alpha_8,
+ * arg gamma_2..gamma_9), the first two-sided Lanczos coefficients (at mu = 0 they vanish
+ * and the prediction is a constant), and predicts (log k*, log l*): the outer dimension at
+ * which the stopping estimate reaches the tolerance and the inner dimension that keeps
+ * the inner estimate below it. Parameters: 5378 floats, W1 [64][16], b1 [64], W2 [64][64],
+ * b2 [64], W3 [2][64], b3 [2] (row-major, out x in). All pointers here are HOST memory.
+ * Training, forward and backward run in the library's own kernels. */
+int ov_mlp_forward(const float* theta, int n, const float* X, float* Y);
+/* loss = mean over the n samples of ||y - Y||^2; grad: 5378 floats (either may be NULL) */
+int ov_mlp_loss_grad(const float* theta, int n, const float* X, const float* Y, float* loss,
+                     float* grad);
+/* Adam (lr; beta 0.9 / 0.999; eps 1e-8) on minibatches of `batch` samples (<= 0: the
+ * whole set), `epochs` passes, reshuffled per epoch with a seeded generator; theta is
+ * updated in place; loss_history (epochs floats, may be NULL) gets the training loss after
+ * each epoch. With n_val > 0 validation samples (Xv, Yv), the loss on them is recorded in
+ * val_history (may be NULL) and theta returns the parameters of the epoch with the lowest
+ * validation loss (early stopping). */
+int ov_mlp_train(float* theta, int n, const float* X, const float* Y, int epochs, int batch,
+                 float lr, unsigned seed, float* loss_history, int n_val, const float* Xv,
+                 const float* Yv, float* val_history);
+/* Attach a trained network to a handle (theta NULL detaches). With it, ov_sign_apply runs
+ * 16 outer steps, predicts (k*, l*) per right-hand side on the device, places the first
+ * stopping check at the smallest predicted k* and uses the predicted l (rounded up to a
+ * multiple of 8, clamped to [l_min, min(l_max, l)]). The a-posteriori estimates still
+ * decide: checks continue past a short prediction, and an inner estimate above tol grows
+ * l by 16 and repeats the check. */
+int ov_set_sizer(ov_handle* h, const float* theta, int l_min, int l_max);
+/* Coefficients of the last ov_sign_apply / ov_apply for right-hand side `rhs`:
+ * alpha_j, beta_j, gamma_j for j = 1..k (complex doubles, host; beta_1 = gamma_1 = 0),
+ * k = min(kcap, steps run) written to *k. H_k has diagonal alpha, subdiagonal
+ * H_{j+1,j} = beta_{j+1} and superdiagonal H_{j,j+1} = gamma_{j+1} (Sec. 2). */
+int ov_get_coefficients(const ov_handle* h, int rhs, int kcap, void* alpha, void* beta,
+                        void* gamma, int* k);
 
 /* Roberts-Higham sign of dense matrices without any device allocation. The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc, such as

@@ -24,4 +24,5 @@ from .gen import (  # noqa: F401
     round_links_fp32,
     problem_batch_48,
     training_problems,
+    problem_source,
 )

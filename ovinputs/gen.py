@@ -127,7 +127,8 @@ def problem_batch_48(seed_base=0):
 
 def training_problems(count=2000, seed_base=1000):
     """Small problems for learning (k, l): 6^4, 6^3x8, 8^3x6, 8^4, mu ~ U[0,0.5],
-    eps ~ U[0.2,0.5], m_w = -1.5, one Gaussian source, seeds seed_base + i."""
+    eps ~ U[0.2,0.5], m_w ~ U[-1.8,-1.3], seeds seed_base + i; the source is a Gaussian
+    (even i) or a spin-colour point source at site 0 (odd i)."""
     shapes = [(6, 6, 6, 6), (6, 6, 6, 8), (8, 8, 8, 6), (8, 8, 8, 8)]
     out = []
     for i in range(count):
@@ -135,6 +136,16 @@ def training_problems(count=2000, seed_base=1000):
         dims = shapes[int(rng.integers(0, 4))]
         mu = float(rng.uniform(0.0, 0.5))
         eps = float(rng.uniform(0.2, 0.5))
-        out.append(dict(dims=dims, kind="near_unit", eps=eps, mu=mu, m_w=-1.5,
-                        gauge_seed=seed_base + i, source_seed=seed_base + i + 100000))
+        m_w = float(rng.uniform(-1.8, -1.3))
+        sc = int(rng.integers(0, 12))
+        out.append(dict(dims=dims, kind="near_unit", eps=eps, mu=mu, m_w=m_w,
+                        gauge_seed=seed_base + i, source_seed=seed_base + i + 100000,
+                        source="gaussian" if i % 2 == 0 else "point", spin=sc // 3, colour=sc % 3))
     return out
+
+
+def problem_source(p):
+    """The source of a problem dict from training_problems / problem_batch_48."""
+    if p.get("source", "gaussian") == "point":
+        return point_source(p["dims"], 0, p["spin"], p["colour"])
+    return gaussian_source(p["dims"], p["source_seed"])

@@ -7,8 +7,15 @@ from .binding import (  # noqa: F401
     Overlap,
     OvError,
     ov_apply,
+    ov_batch_create,
+    ov_batch_sign_apply,
     ov_create,
     ov_default_opts,
+    ov_get_coefficients,
+    ov_mlp_forward,
+    ov_mlp_loss_grad,
+    ov_mlp_train,
+    ov_set_sizer,
     ov_destroy,
     ov_get_stats,
     ov_reset_stats,

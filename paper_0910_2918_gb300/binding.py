@@ -44,7 +44,7 @@ class ov_opts(ctypes.Structure):
     _fields_ = [("check_interval", ctypes.c_int), ("first_check", ctypes.c_int),
                 ("recombination", ctypes.c_int), ("rh_tol", ctypes.c_double), ("rh_maxit", ctypes.c_int),
                 ("breakdown_tol", ctypes.c_double), ("inner_dl", ctypes.c_int), ("k_fixed", ctypes.c_int),
-                ("check_schedule", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("check_schedule", ctypes.c_int), ("block_size", ctypes.c_int), ("timing", ctypes.c_int)]
 
 
 class ov_stats(ctypes.Structure):
@@ -53,7 +53,7 @@ class ov_stats(ctypes.Structure):
                 ("other_launches", ctypes.c_longlong), ("stencil_ms", ctypes.c_double),
                 ("update_ms", ctypes.c_double), ("inner_ms", ctypes.c_double), ("recombine_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("outer_steps", ctypes.c_longlong),
-                ("regen_steps", ctypes.c_longlong), ("checks", ctypes.c_longlong)]
+                ("regen_steps", ctypes.c_longlong), ("checks", ctypes.c_longlong), ("block_size", ctypes.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -105,12 +105,31 @@ def lib():
         f.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                       ctypes.POINTER(ov_info)]
         f.restype = ctypes.c_int
+    L.ov_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ov_geom), ctypes.POINTER(vp),
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ov_opts), vp]
+    L.ov_batch_create.restype = ctypes.c_int
+    L.ov_batch_sign_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(ov_info)]
+    L.ov_batch_sign_apply.restype = ctypes.c_int
     L.ov_wilson_apply.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int]
     L.ov_wilson_apply.restype = ctypes.c_int
     L.ov_inner_sign.argtypes = [vp, ctypes.c_int, ctypes.c_int, ip, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, dp, ip]
     L.ov_inner_sign.restype = ctypes.c_int
     L.ov_rh_sign.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ip]
     L.ov_rh_sign.restype = ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.ov_mlp_forward.argtypes = [fp, ctypes.c_int, fp, fp]
+    L.ov_mlp_forward.restype = ctypes.c_int
+    L.ov_mlp_loss_grad.argtypes = [fp, ctypes.c_int, fp, fp, fp, fp]
+    L.ov_mlp_loss_grad.restype = ctypes.c_int
+    L.ov_mlp_train.argtypes = [fp, ctypes.c_int, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint, fp,
+                               ctypes.c_int, fp, fp, fp]
+    L.ov_mlp_train.restype = ctypes.c_int
+    L.ov_set_sizer.argtypes = [vp, fp, ctypes.c_int, ctypes.c_int]
+    L.ov_set_sizer.restype = ctypes.c_int
+    L.ov_get_coefficients.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, ip]
+    L.ov_get_coefficients.restype = ctypes.c_int
     L.ov_rh_sign_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, ip, ctypes.c_double, ctypes.c_int, vp]
     L.ov_rh_sign_noalloc.restype = ctypes.c_int
     L.ov_version.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -319,6 +338,141 @@ def ov_rh_sign_noalloc(T, S, rh_tol=1e-10, rh_maxit=100, stream=None):
     return rc, its
 
 
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+MLP_PARAMS = 5378
+
+
+def ov_mlp_forward(theta, X):
+    """Sizing network forward pass on the GPU: X (n, 16) -> (n, 2)."""
+    theta = _f32(theta, (MLP_PARAMS,))
+    X = _f32(X)
+    Y = np.zeros((X.shape[0], 2), dtype=np.float32)
+    rc = lib().ov_mlp_forward(_fp(theta), X.shape[0], _fp(X), _fp(Y))
+    if rc != OV_OK:
+        raise OvError(rc, "ov_mlp_forward")
+    return Y
+
+
+def ov_mlp_loss_grad(theta, X, Y):
+    theta = _f32(theta, (MLP_PARAMS,))
+    X, Y = _f32(X), _f32(Y)
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.zeros(MLP_PARAMS, dtype=np.float32)
+    rc = lib().ov_mlp_loss_grad(_fp(theta), X.shape[0], _fp(X), _fp(Y), _fp(loss), _fp(grad))
+    if rc != OV_OK:
+        raise OvError(rc, "ov_mlp_loss_grad")
+    return float(loss[0]), grad
+
+
+def ov_mlp_train(theta, X, Y, epochs, batch=0, lr=1e-3, seed=1, Xv=None, Yv=None):
+    """Train on the GPU (Adam); returns (theta, training loss per epoch) or, with validation
+    data, (theta of the best validation epoch, training losses, validation losses)."""
+    th = _f32(theta, (MLP_PARAMS,)).copy()
+    X, Y = _f32(X), _f32(Y)
+    hist = np.zeros(epochs, dtype=np.float32)
+    if Xv is None:
+        rc = lib().ov_mlp_train(_fp(th), X.shape[0], _fp(X), _fp(Y), int(epochs), int(batch), float(lr), int(seed),
+                                _fp(hist), 0, None, None, None)
+        if rc != OV_OK:
+            raise OvError(rc, "ov_mlp_train")
+        return th, hist
+    Xv, Yv = _f32(Xv), _f32(Yv)
+    vh = np.zeros(epochs, dtype=np.float32)
+    rc = lib().ov_mlp_train(_fp(th), X.shape[0], _fp(X), _fp(Y), int(epochs), int(batch), float(lr), int(seed),
+                            _fp(hist), Xv.shape[0], _fp(Xv), _fp(Yv), _fp(vh))
+    if rc != OV_OK:
+        raise OvError(rc, "ov_mlp_train")
+    return th, hist, vh
+
+
+def ov_set_sizer(h, theta, l_min=8, l_max=120):
+    if theta is None:
+        rc = lib().ov_set_sizer(ctypes.c_void_p(h), None, int(l_min), int(l_max))
+    else:
+        th = _f32(theta, (MLP_PARAMS,))
+        rc = lib().ov_set_sizer(ctypes.c_void_p(h), _fp(th), int(l_min), int(l_max))
+    if rc != OV_OK:
+        raise OvError(rc, "ov_set_sizer")
+
+
+def ov_get_coefficients(h, rhs, kcap):
+    """(alpha, beta, gamma) of the last apply for one RHS, index 0 = step 1."""
+    a = np.zeros(kcap, dtype=np.complex128)
+    b = np.zeros(kcap, dtype=np.complex128)
+    g = np.zeros(kcap, dtype=np.complex128)
+    k = ctypes.c_int(0)
+    rc = lib().ov_get_coefficients(ctypes.c_void_p(h), int(rhs), int(kcap), a.ctypes.data, b.ctypes.data,
+                                   g.ctypes.data, ctypes.byref(k))
+    if rc != OV_OK:
+        raise OvError(rc, "ov_get_coefficients")
+    return a[:k.value], b[:k.value], g[:k.value]
+
+
+def ov_batch_create(dims_list, links_list, m_w_list, mu_list, precision="fp32", t_antiperiodic=True, opts=None,
+                    stream=None):
+    """Handle for a batch of independent lattices (one source each)."""
+    n = len(dims_list)
+    geoms = (ov_geom * n)()
+    keep = []
+    ptrs = (ctypes.c_void_p * n)()
+    mem = None
+    for i in range(n):
+        for d in range(4):
+            geoms[i].dims[d] = int(dims_list[i][d])
+        geoms[i].precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        geoms[i].t_antiperiodic = 1 if t_antiperiodic else 0
+        _check_c128(links_list[i], "links")
+        p, m = _ptr_mem(links_list[i])
+        if mem is None:
+            mem = m
+        elif m != mem:
+            raise ValueError("links must all be host or all device arrays")
+        ptrs[i] = p.value
+        keep.append(links_list[i])
+    mw = (ctypes.c_double * n)(*[float(v) for v in m_w_list])
+    mu = (ctypes.c_double * n)(*[float(v) for v in mu_list])
+    h = ctypes.c_void_p()
+    rc = lib().ov_batch_create(ctypes.byref(h), n, geoms, ptrs, mem, mw, mu,
+                               ctypes.byref(opts) if opts is not None else None,
+                               ctypes.c_void_p(stream) if stream is not None else None)
+    if rc != OV_OK:
+        raise OvError(rc, "ov_batch_create")
+    return h.value
+
+
+def ov_batch_sign_apply(h, xs, ys, tol, k_max, l):
+    """xs, ys: lists of complex128 arrays (all host numpy or all CUDA tensors)."""
+    n = len(xs)
+    xp = (ctypes.c_void_p * n)()
+    yp = (ctypes.c_void_p * n)()
+    mem = None
+    for i in range(n):
+        _check_c128(xs[i], "x")
+        _check_c128(ys[i], "y")
+        p, m = _ptr_mem(xs[i])
+        q, m2 = _ptr_mem(ys[i], writable=True)
+        if m != m2 or (mem is not None and m != mem):
+            raise ValueError("x and y must all be host or all device arrays")
+        mem = m
+        xp[i] = p.value
+        yp[i] = q.value
+    infos = (ov_info * n)()
+    rc = lib().ov_batch_sign_apply(ctypes.c_void_p(h), xp, yp, mem, float(tol), int(k_max), int(l), infos)
+    if rc < 0:
+        raise OvError(rc, "ov_batch_sign_apply")
+    return rc, [i.as_dict() for i in infos]
+
+
 class Overlap:
     """Owner of one handle: y = sgn(gamma5 D_w(mu)) x and D_ov(mu) x for one gauge field."""
 
@@ -348,6 +502,12 @@ class Overlap:
 
     def stats(self):
         return ov_get_stats(self.h)
+
+    def set_sizer(self, theta, l_min=8, l_max=120):
+        ov_set_sizer(self.h, theta, l_min, l_max)
+
+    def coefficients(self, rhs, kcap):
+        return ov_get_coefficients(self.h, rhs, kcap)
 
     def reset_stats(self):
         ov_reset_stats(self.h)

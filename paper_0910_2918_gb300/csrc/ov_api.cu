@@ -20,6 +20,7 @@
 #include <chrono>
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "ov_internal.h"
@@ -28,7 +29,8 @@ using namespace ov;
 
 namespace {
 
-constexpr int kChunk = 64;  // outer basis slots per allocation chunk
+constexpr int kChunk = 64;       // outer basis slots per allocation chunk
+constexpr int kSizerSteps = 16;  // outer steps whose coefficients feed the learned sizing
 
 struct Buf {
   void* p = nullptr;
@@ -56,21 +58,37 @@ void release(Buf& b) {
 
 }  // namespace
 
+struct TuneKey {
+  int prec, mode, nprob, pad;
+  bool operator<(const TuneKey& o) const {
+    return prec != o.prec ? prec < o.prec : (mode != o.mode ? mode < o.mode : nprob < o.nprob);
+  }
+};
+
+// one gauge field with its operator parameters
+struct Lattice {
+  Geometry g{};
+  Buf links;
+  double m_w = -1.5, mu = 0.0;
+};
+
 struct ov_handle {
   int dev = 0;
   cudaStream_t st = nullptr;
-  Geometry g{};
   int prec = OV_PREC_FP64;
   int antiperiodic = 1;
-  double m_w = -1.5, mu = 0.0;
   ov_opts o{};
-  Buf links;
+  // a single-field handle has one lattice and any number of right-hand sides per call;
+  // a batch handle (ov_batch_create) has one lattice per problem and one source each
+  std::vector<Lattice> lat;
+  int is_batch = 0;
+  Buf desc, blkmap;  // device problem descriptors and block -> problem map of the current call
   // outer level
   Buf xcanon, ycanon;             // canonical device copies for host buffers
   Buf tv, tw, p, r, vring, wring;  // [nrhs][12V] vectors (rings hold 2 slots)
   Buf yacc;                       // two-pass accumulator
   std::vector<Buf> chunks;        // stored basis: chunk c holds slots c*kChunk.. [slot][rhs][12V]
-  int chunk_rhs = 0;              // nrhs the chunks were sized for
+  size_t chunk_pool = 0;          // vector-pool bytes the chunks were sized for
   Buf coef_alp, coef_bet, coef_gam, coef_nv, coef_nw, coef_status, coef_kbreak;
   Buf partials, counters, scale, scal;
   int cap_rhs = 0, cap_ld = 0;
@@ -80,6 +98,12 @@ struct ov_handle {
   Buf vptr;  // device array of basis slot pointers for recombination
   int inner_cap = 0, inner_ld = 0;
   ov_stats stats{};
+  std::map<TuneKey, int> tuned;  // autotuned block size per (precision, mode, problem count)
+  // learned sizing
+  Buf sizer_theta, sizer_feat, sizer_pred;
+  int sizer_on = 0, sizer_lmin = 8, sizer_lmax = kMaxL;
+  // the last apply (for ov_get_coefficients)
+  int last_steps = 0, last_ld = 0, last_nrhs = 0;
   int trace = 0;  // OV_TRACE set in the environment: one JSON line per check on stderr
   // event pairs recorded around timed launches: (class, start, stop)
   std::vector<cudaEvent_t> ev_pool;
@@ -147,7 +171,53 @@ extern "C" int ov_reset_stats(ov_handle* h) {
     }                                                  \
   } while (0)
 
-static size_t vec_bytes(const ov_handle* h) { return vec_elem_bytes(h->prec) * 12 * (size_t)h->g.V; }
+// Problem descriptors of one call: problem r uses lattice lat_of[r]; vectors are pooled
+// (12 V_r complex entries per problem, in problem order). Uploads the descriptors and the
+// block map and returns the batch description and the pool size in complex entries.
+static int build_batch(ov_handle* h, const std::vector<int>& lat_of, int bs, Batch* b, size_t* pool) {
+  const int np = (int)lat_of.size();
+  std::vector<ProbDesc> d(np);
+  std::vector<int> map;
+  size_t voff = 0;
+  int blk = 0;
+  for (int r = 0; r < np; ++r) {
+    const Lattice& L = h->lat[lat_of[r]];
+    d[r].g = L.g;
+    d[r].links = L.links.p;
+    fill_consts(d[r], L.m_w, L.mu);
+    d[r].voff = voff;
+    d[r].block0 = blk;
+    d[r].nblk = num_site_blocks(L.g, bs);
+    voff += 12 * (size_t)L.g.V;
+    blk += d[r].nblk;
+    for (int q = 0; q < d[r].nblk; ++q) map.push_back(r);
+  }
+  CK(grow(h->desc, sizeof(ProbDesc) * np));
+  CK(grow(h->blkmap, sizeof(int) * map.size()));
+  CK(cudaMemcpyAsync(h->desc.p, d.data(), sizeof(ProbDesc) * np, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->blkmap.p, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, h->st));
+  b->desc = (const ProbDesc*)h->desc.p;
+  b->blk_prob = (const int*)h->blkmap.p;
+  b->nblocks = blk;
+  b->nprob = np;
+  b->block = bs;
+  *pool = voff;
+  return OV_OK;
+}
+
+// site blocks of a call at the smallest block size (sizes the partial-sum buffer)
+static int max_blocks(const ov_handle* h, const std::vector<int>& lat_of) {
+  int n = 0;
+  for (int q : lat_of) n += num_site_blocks(h->lat[q].g, 64);
+  return n;
+}
+
+static std::vector<int> lattices_of_call(const ov_handle* h, int nprob) {
+  std::vector<int> v(nprob, 0);
+  if (h->is_batch)
+    for (int r = 0; r < nprob; ++r) v[r] = r;
+  return v;
+}
 
 extern "C" void ov_default_opts(ov_opts* o) {
   if (!o) return;
@@ -160,6 +230,7 @@ extern "C" void ov_default_opts(ov_opts* o) {
   o->inner_dl = 4;
   o->k_fixed = 0;
   o->check_schedule = 0;
+  o->block_size = 0;
   o->timing = 0;
 }
 
@@ -180,7 +251,8 @@ extern "C" const char* ov_strerror(int code) {
 static int check_opts(const ov_opts& o) {
   if (o.check_interval < 1 || o.rh_maxit < 1 || !(o.rh_tol > 0) || o.inner_dl < 1 || o.k_fixed < 0 ||
       o.first_check < 0 || o.recombination < 0 || o.recombination > 2 || !(o.breakdown_tol >= 0) ||
-      o.check_schedule < 0 || o.check_schedule > 1)
+      o.check_schedule < 0 || o.check_schedule > 1 ||
+      (o.block_size != 0 && o.block_size != 64 && o.block_size != 128 && o.block_size != 256))
     return OV_ERR_ARG;
   return OV_OK;
 }
@@ -232,11 +304,13 @@ extern "C" int ov_create(ov_handle** hp, const ov_geom* geom, const void* links,
   ov_handle* h = new ov_handle();
   CK(cudaGetDevice(&h->dev));
   h->st = (cudaStream_t)stream;
-  h->g = Geometry{(int)V, geom->dims[0], geom->dims[1], geom->dims[2], geom->dims[3]};
+  h->lat.resize(1);
+  Lattice& L = h->lat[0];
+  L.g = Geometry{(int)V, geom->dims[0], geom->dims[1], geom->dims[2], geom->dims[3]};
+  L.m_w = m_w;
+  L.mu = mu;
   h->prec = geom->precision;
   h->antiperiodic = geom->t_antiperiodic ? 1 : 0;
-  h->m_w = m_w;
-  h->mu = mu;
   h->o = o;
   h->trace = getenv("OV_TRACE") != nullptr;
   const size_t canon = sizeof(double2) * 36 * (size_t)V;
@@ -253,12 +327,12 @@ extern "C" int ov_create(ov_handle** hp, const ov_geom* geom, const void* links,
     src = (const double2*)tmp.p;
   }
   const size_t lb = (h->prec == OV_PREC_FP64 ? sizeof(double2) : sizeof(float2)) * 36 * (size_t)V;
-  if (grow(h->links, lb) != cudaSuccess) return fail(OV_ERR_NOMEM);
+  if (grow(L.links, lb) != cudaSuccess) return fail(OV_ERR_NOMEM);
   const int nb = (int)((V + 127) / 128);
   if (h->prec == OV_PREC_FP64)
-    k_links<double2><<<nb, 128, 0, h->st>>>(h->g, h->antiperiodic, src, (double2*)h->links.p);
+    k_links<double2><<<nb, 128, 0, h->st>>>(L.g, h->antiperiodic, src, (double2*)L.links.p);
   else
-    k_links<float2><<<nb, 128, 0, h->st>>>(h->g, h->antiperiodic, src, (float2*)h->links.p);
+    k_links<float2><<<nb, 128, 0, h->st>>>(L.g, h->antiperiodic, src, (float2*)L.links.p);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->st) != cudaSuccess) return fail(OV_ERR_CUDA);
   release(tmp);
   *hp = h;
@@ -269,12 +343,13 @@ extern "C" void ov_destroy(ov_handle* h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   if (h->st) cudaStreamSynchronize(h->st);
-  Buf* all[] = {&h->links, &h->xcanon, &h->ycanon, &h->tv, &h->tw, &h->p, &h->r, &h->vring, &h->wring, &h->yacc,
+  for (Lattice& L : h->lat) release(L.links);
+  Buf* all[] = {&h->desc, &h->blkmap, &h->xcanon, &h->ycanon, &h->tv, &h->tw, &h->p, &h->r, &h->vring, &h->wring, &h->yacc,
                 &h->coef_alp, &h->coef_bet, &h->coef_gam, &h->coef_nv, &h->coef_nw, &h->coef_status,
                 &h->coef_kbreak, &h->partials, &h->counters, &h->scale, &h->scal, &h->iQ, &h->iT, &h->ileff, &h->iS, &h->is,
                 &h->irh_its, &h->irh_ok, &h->iperm, &h->ifail, &h->ck, &h->cl, &h->ckprev, &h->cc_cur, &h->cc_prev,
                 &h->cc_fin, &h->cacc_cur, &h->cacc_fin, &h->c_est_in, &h->c_est_out, &h->c_rhst, &h->c_rhit,
-                &h->vptr};
+                &h->vptr, &h->sizer_theta, &h->sizer_feat, &h->sizer_pred};
   for (Buf* b : all) release(*b);
   for (Buf& b : h->chunks) release(b);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -282,8 +357,8 @@ extern "C" void ov_destroy(ov_handle* h) {
 }
 
 // ---------------------------------------------------------------- workspace
-static int ensure_outer(ov_handle* h, int nrhs, int ld) {
-  const size_t vb = vec_bytes(h) * nrhs;
+static int ensure_outer(ov_handle* h, int nrhs, int ld, size_t pool, int nblocks) {
+  const size_t vb = vec_elem_bytes(h->prec) * pool;
   CK(grow(h->tv, vb));
   CK(grow(h->tw, vb));
   CK(grow(h->p, vb));
@@ -298,7 +373,7 @@ static int ensure_outer(ov_handle* h, int nrhs, int ld) {
   CK(grow(h->coef_nv, sizeof(double) * (size_t)nrhs * ld));
   CK(grow(h->coef_status, sizeof(int) * nrhs));
   CK(grow(h->coef_kbreak, sizeof(int) * nrhs));
-  CK(grow(h->partials, sizeof(double) * 4 * (size_t)nrhs * num_site_blocks(h->g)));
+  CK(grow(h->partials, sizeof(double) * 4 * (size_t)nblocks));
   if (h->counters.bytes < sizeof(unsigned) * nrhs) {
     CK(grow(h->counters, sizeof(unsigned) * nrhs));
     CK(cudaMemsetAsync(h->counters.p, 0, sizeof(unsigned) * nrhs, h->st));
@@ -369,23 +444,23 @@ static Coefs coefs(ov_handle* h, int ld) {
 }
 
 // pointer to basis slot `slot` (0-based, = step j - 1), allocating chunks on demand
-static int basis_slot(ov_handle* h, int nrhs, int slot, void** out) {
-  if (h->chunk_rhs != nrhs) {
+static int basis_slot(ov_handle* h, size_t pool_bytes, int slot, void** out) {
+  if (h->chunk_pool != pool_bytes) {
     for (Buf& b : h->chunks) release(b);
     h->chunks.clear();
-    h->chunk_rhs = nrhs;
+    h->chunk_pool = pool_bytes;
   }
   const int c = slot / kChunk;
   while ((int)h->chunks.size() <= c) {
     Buf b;
-    cudaError_t e = grow(b, vec_bytes(h) * nrhs * kChunk);
+    cudaError_t e = grow(b, pool_bytes * kChunk);
     if (e != cudaSuccess) {
       cudaGetLastError();  // clear the allocation error
       return OV_ERR_NOMEM;
     }
     h->chunks.push_back(b);
   }
-  *out = (char*)h->chunks[c].p + vec_bytes(h) * nrhs * (size_t)(slot % kChunk);
+  *out = (char*)h->chunks[c].p + pool_bytes * (size_t)(slot % kChunk);
   return OV_OK;
 }
 
@@ -400,16 +475,31 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   if (ktarget > kMaxInnerK) return OV_ERR_TOO_LARGE;
   CK(cudaSetDevice(h->dev));
   cudaStream_t st = h->st;
-  const Geometry& g = h->g;
-  const bool herm = h->mu == 0.0;
+  if (h->is_batch && nrhs != (int)h->lat.size()) return OV_ERR_ARG;
+  const std::vector<int> lat_of = lattices_of_call(h, nrhs);
+  bool herm = true;
+  for (int q : lat_of) herm = herm && h->lat[q].mu == 0.0;
   const int mode = herm ? kModeLanczos : kModeTwoSided;
   const int ld = ktarget + 2;
-  int rc = ensure_outer(h, nrhs, ld);
+  Batch bt;
+  size_t pool = 0;
+  // block size: forced by opts.block_size, else the tuned one for this problem set, else
+  // tuned below at the first step
+  const TuneKey key{h->prec, mode, nrhs, 0};
+  int bs = o.block_size;
+  bool tune = false;
+  if (bs == 0) {
+    auto it = h->tuned.find(key);
+    if (it != h->tuned.end()) bs = it->second;
+    else { bs = kBlockDefault; tune = true; }
+  }
+  int rc = build_batch(h, lat_of, bs, &bt, &pool);
+  if (rc != OV_OK) return rc;
+  rc = ensure_outer(h, nrhs, ld, pool, max_blocks(h, lat_of));
   if (rc != OV_OK) return rc;
   rc = ensure_inner(h, nrhs, ld);
   if (rc != OV_OK) return rc;
-  const size_t n12 = 12 * (size_t)g.V;
-  const size_t canon = sizeof(double2) * n12 * nrhs;
+  const size_t canon = sizeof(double2) * pool;
   const double2* xd = (const double2*)x;
   double2* yd = (double2*)y;
   if (mem == OV_MEM_HOST) {
@@ -420,16 +510,14 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     yd = (double2*)h->ycanon.p;
   }
   Coefs c = coefs(h, ld);
-  const size_t vb1 = vec_bytes(h);
-  const size_t vbn = vb1 * nrhs;
+  const size_t vbn = vec_elem_bytes(h->prec) * pool;  // one vector of every problem
   CK(cudaMemsetAsync(c.alp, 0, sizeof(double2) * (size_t)nrhs * ld, st));
   CK(cudaMemsetAsync(c.bet, 0, sizeof(double2) * (size_t)nrhs * ld, st));
   CK(cudaMemsetAsync(c.gam, 0, sizeof(double2) * (size_t)nrhs * ld, st));
   CK(cudaMemsetAsync(h->vring.p, 0, 2 * vbn, st));
   CK(cudaMemsetAsync(h->wring.p, 0, 2 * vbn, st));
   // v_1 = w_1 = x / ||x||: x goes to tv (and tw), the norm into nv_1 / nw_1
-  CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 1,
-                 h->scal.p, st));
+  CK(launch_pack(h->prec, bt, xd, h->tv.p, c, (double*)h->partials.p, (unsigned*)h->counters.p, 1, h->scal.p, st));
   if (!herm) CK(cudaMemcpyAsync(h->tw.p, h->tv.p, vbn, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpy2DAsync(h->scale.p, sizeof(double), (double*)c.nv + 1, sizeof(double) * ld, sizeof(double), nrhs,
                        cudaMemcpyDeviceToDevice, st));
@@ -446,22 +534,12 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   }
 
   StepArgs a{};
-  a.g = g;
-  a.nrhs = nrhs;
-  a.links = h->links.p;
-  a.mass = h->m_w + 4.0;
-  a.emu = exp(h->mu);
-  a.emui = exp(-h->mu);
-  split_const(a.mass, a.mass_hl);
-  split_const(a.emu, a.emu_hl);
-  split_const(a.emui, a.emui_hl);
+  a.b = bt;
   a.scal = h->scal.p;
   a.tv = h->tv.p;
   a.tw = h->tw.p;
   a.p = h->p.p;
   a.r = h->r.p;
-  a.s_tv = a.s_tw = a.s_p = a.s_r = n12;
-  a.s_vprev = a.s_vcur = a.s_wprev = a.s_wcur = n12;
   a.c = c;
   a.breakdown_tol = o.breakdown_tol;
   a.partials = (double*)h->partials.p;
@@ -490,7 +568,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   for (j = 1; j <= ktarget && ndone < nrhs; ++j) {
     void* vcur = nullptr;
     if (recomb == OV_RECOMB_STORED) {
-      rc = basis_slot(h, nrhs, j - 1, &vcur);
+      rc = basis_slot(h, vbn, j - 1, &vcur);
       if (rc != OV_OK) {
         if (o.recombination != OV_RECOMB_AUTO) return rc;
         recomb = OV_RECOMB_TWO_PASS;  // out of memory: fall back to the double pass
@@ -506,6 +584,42 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     if (j == 1) {
       CK(cudaMemsetAsync((char*)h->wring.p + vbn, 0, vbn, st));
     }
+    if (j == 1 && tune) {
+      // autotune the block size on the first step (it only reads x and the step-1
+      // scalars, so re-running it is harmless): best of two timed launches per size
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      float best = 1e30f;
+      int best_bs = kBlockDefault;
+      for (int cand : {64, 128, 256}) {
+        Batch bc;
+        size_t pc = 0;
+        rc = build_batch(h, lat_of, cand, &bc, &pc);
+        if (rc != OV_OK) return rc;
+        a.b = bc;
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          CK(cudaEventRecord(e0, st));
+          CK(launch_step(h->prec, mode, a, st));
+          CK(cudaEventRecord(e1, st));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          tmin = std::min(tmin, ms);
+        }
+        h->stats.launches += 2;
+        if (tmin < best) { best = tmin; best_bs = cand; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      h->tuned[key] = best_bs;
+      rc = build_batch(h, lat_of, best_bs, &bt, &pool);
+      if (rc != OV_OK) return rc;
+      a.b = bt;
+      if (h->trace) fprintf(stderr, "{\"ov_autotune\": %d, \"ms\": %.4f}\n", best_bs, best);
+    }
+    h->stats.block_size = a.b.block;
     int ts = tstart(h, kClsStencil);
     CK(launch_step(h->prec, mode, a, st));
     tstop(h, ts);
@@ -518,6 +632,44 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     h->stats.outer_steps += 1;
     prev_v = vcur;
     const bool fixed = o.k_fixed > 0;
+    if (h->sizer_on && !fixed && j == kSizerSteps && ktarget > kSizerSteps + 1) {
+      // learned sizing: f = (Im alpha_1..alpha_8, arg gamma_2..gamma_9) -> (log k*, log l*)
+      std::vector<double2> fa((size_t)nrhs * 8), fg((size_t)nrhs * 8);
+      CK(cudaMemcpy2DAsync(fa.data(), sizeof(double2) * 8, c.alp + 1, sizeof(double2) * ld, sizeof(double2) * 8, nrhs,
+                           cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpy2DAsync(fg.data(), sizeof(double2) * 8, c.gam + 2, sizeof(double2) * ld, sizeof(double2) * 8, nrhs,
+                           cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      std::vector<float> feat((size_t)nrhs * 16), pred((size_t)nrhs * 2);
+      for (int r = 0; r < nrhs; ++r)
+        for (int i = 0; i < 8; ++i) {
+          feat[(size_t)r * 16 + i] = (float)fa[(size_t)r * 8 + i].y;
+          const double2 gg = fg[(size_t)r * 8 + i];
+          feat[(size_t)r * 16 + 8 + i] = (float)std::atan2(gg.y, gg.x);
+        }
+      CK(grow(h->sizer_feat, sizeof(float) * feat.size()));
+      CK(grow(h->sizer_pred, sizeof(float) * pred.size()));
+      CK(cudaMemcpyAsync(h->sizer_feat.p, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, st));
+      CK(mlp_predict_device((const float*)h->sizer_theta.p, nrhs, (const float*)h->sizer_feat.p,
+                            (float*)h->sizer_pred.p, st));
+      CK(cudaMemcpyAsync(pred.data(), h->sizer_pred.p, sizeof(float) * pred.size(), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      h->stats.launches += 1;
+      // the right-hand sides advance together until the last one stops, so the first
+      // check goes to the largest predicted k*
+      double kmax_pred = -1.0;
+      for (int r = 0; r < nrhs; ++r) {
+        const double kp = std::exp((double)pred[(size_t)r * 2]);
+        const double lp = std::exp((double)pred[(size_t)r * 2 + 1]);
+        if (std::isfinite(kp)) kmax_pred = std::max(kmax_pred, kp);
+        int lr = std::isfinite(lp) ? ((int)std::ceil(lp / 8.0)) * 8 : h->sizer_lmax;
+        lreq[r] = std::max(h->sizer_lmin, std::min(lr, std::min(h->sizer_lmax, std::min(l, kMaxL))));
+      }
+      CK(cudaMemcpyAsync(h->cl.p, lreq.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+      if (kmax_pred > 0.0) next_check = std::max(j + 1, std::min((int)std::floor(kmax_pred), ktarget));
+      if (h->trace)
+        fprintf(stderr, "{\"ov_sizer\": %d, \"k_pred_max\": %.1f, \"l_req0\": %d}\n", j, kmax_pred, lreq[0]);
+    }
     const bool check = fixed ? (j == ktarget) : (j >= next_check || j == ktarget);
     if (!check) continue;
     // read the breakdown state first: a Lanczos breakdown fixes k for that RHS
@@ -527,6 +679,9 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     for (int r = 0; r < nrhs; ++r) kcur[r] = (dstatus[r] != kStOK && dkbreak[r] > 0) ? std::min(dkbreak[r], j) : j;
     CK(cudaMemcpyAsync(h->ck.p, kcur.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(h->ckprev.p, kprev.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    bool regrow = false;
+    do {
+    regrow = false;
     const auto tc0 = std::chrono::steady_clock::now();
     const int ti = tstart(h, kClsInner);
     cudaError_t e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, ld, iw,
@@ -604,6 +759,12 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
       } else {
         if (lucky) est = 0.0;
         if (est <= tol || lucky || j == ktarget) {
+          // with learned sizing, an inner estimate above tol grows l and re-checks
+          if (h->sizer_on && ei[r] > tol && lreq[r] < std::min(h->sizer_lmax, std::min(kcur[r], kMaxL))) {
+            lreq[r] = std::min(lreq[r] + 16, std::min(h->sizer_lmax, kMaxL));
+            regrow = true;
+            continue;
+          }
           fin = 1;
           est = std::max(est, ei[r]);
           sr = est <= tol ? OV_OK : OV_NOT_CONVERGED;
@@ -639,6 +800,8 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
         }
       }
     }
+    if (regrow) CK(cudaMemcpyAsync(h->cl.p, lreq.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    } while (regrow);
     std::swap(h->cc_cur, h->cc_prev);
     // next check: fixed interval, or (adaptive) a jump to where the log-linear decay of
     // the error reaches tol, always followed by a partner check check_interval later
@@ -650,8 +813,9 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
         if (done[r] || he1[r] <= 0.0 || he2[r] <= 0.0 || he2[r] >= he1[r] || tol <= 0.0 || hk2[r] <= hk1[r]) continue;
         const double rate = (std::log(he2[r]) - std::log(he1[r])) / (hk2[r] - hk1[r]);
         const double ks = hk2[r] + (std::log(tol) - std::log(he2[r])) / rate;
+        // the batch runs until its slowest right-hand side stops: aim at the largest k*
         const int ahead = (int)std::ceil(ks) - j;
-        if (pred < 0 || ahead < pred) pred = ahead;
+        if (ahead > pred) pred = ahead;
       }
       if (pred > step) step = std::min(pred, 10 * o.check_interval);
     }
@@ -659,28 +823,28 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     next_check = j + step;
   }
   const int kmax_used = *std::max_element(kfin.begin(), kfin.end());
+  h->last_steps = j - 1;
+  h->last_ld = ld;
+  h->last_nrhs = nrhs;
   // recombination
   CK(cudaMemcpyAsync(h->ck.p, kfin.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
   const int tr = tstart(h, kClsRecomb);
   if (recomb == OV_RECOMB_STORED) {
     CK(grow(h->vptr, sizeof(void*) * std::max<size_t>(slots.size(), 1)));
     CK(cudaMemcpyAsync(h->vptr.p, slots.data(), sizeof(void*) * slots.size(), cudaMemcpyHostToDevice, st));
-    CK(launch_recombine(h->prec, g, nrhs, (const void* const*)h->vptr.p, n12, h->cacc_fin.p, ld,
-                        (const int*)h->ck.p, (const double*)h->scale.p, xd, add_x, yd, st));
+    CK(launch_recombine(h->prec, bt, (const void* const*)h->vptr.p, h->cacc_fin.p, ld, (const int*)h->ck.p,
+                        (const double*)h->scale.p, xd, add_x, yd, st));
     h->stats.launches += 1;
     h->stats.other_launches += 1;
   } else {
     // second pass: regenerate v_j from the stored coefficients and accumulate y += c_j v_j
-    const size_t ab = acc_elem_bytes(h->prec) * n12 * nrhs;
+    const size_t ab = acc_elem_bytes(h->prec) * pool;
     CK(grow(h->yacc, ab));
     CK(cudaMemsetAsync(h->yacc.p, 0, ab, st));
-    CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0,
-                   nullptr, st));
+    CK(launch_pack(h->prec, bt, xd, h->tv.p, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, nullptr, st));
     CK(cudaMemsetAsync(h->vring.p, 0, 2 * vbn, st));
     StepArgs b = a;
     b.yacc = h->yacc.p;
-    b.s_yacc = n12;
-    b.s_tnext = n12;
     b.cacc = h->cacc_fin.p;
     void* tcur = h->tv.p;
     void* tnxt = h->p.p;
@@ -696,7 +860,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
       std::swap(tcur, tnxt);
       vprev2 = vc;
     }
-    CK(launch_finish_acc(h->prec, g, nrhs, h->yacc.p, n12, (const double*)h->scale.p, xd, add_x, yd, st));
+    CK(launch_finish_acc(h->prec, bt, h->yacc.p, (const double*)h->scale.p, xd, add_x, yd, st));
     h->stats.launches += kmax_used + 2;
     h->stats.stencil_launches += kmax_used;
     h->stats.regen_steps += kmax_used;
@@ -737,13 +901,17 @@ extern "C" int ov_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem,
 extern "C" int ov_wilson_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, int dagger) {
   if (!h || !x || !y || nrhs < 1) return OV_ERR_ARG;
   if (mem != OV_MEM_HOST && mem != OV_MEM_DEVICE) return OV_ERR_ARG;
+  if (h->is_batch && nrhs != (int)h->lat.size()) return OV_ERR_ARG;
   CK(cudaSetDevice(h->dev));
   cudaStream_t st = h->st;
-  const Geometry& g = h->g;
-  int rc = ensure_outer(h, nrhs, std::max(h->cap_ld, 4));
+  Batch bt;
+  size_t pool = 0;
+  const std::vector<int> lat_of = lattices_of_call(h, nrhs);
+  int rc = build_batch(h, lat_of, h->o.block_size ? h->o.block_size : kBlockDefault, &bt, &pool);
   if (rc != OV_OK) return rc;
-  const size_t n12 = 12 * (size_t)g.V;
-  const size_t canon = sizeof(double2) * n12 * nrhs;
+  rc = ensure_outer(h, nrhs, std::max(h->cap_ld, 4), pool, max_blocks(h, lat_of));
+  if (rc != OV_OK) return rc;
+  const size_t canon = sizeof(double2) * pool;
   const double2* xd = (const double2*)x;
   double2* yd = (double2*)y;
   if (mem == OV_MEM_HOST) {
@@ -754,28 +922,89 @@ extern "C" int ov_wilson_apply(ov_handle* h, int nrhs, const void* x, void* y, i
     yd = (double2*)h->ycanon.p;
   }
   Coefs c = coefs(h, h->cap_ld);
-  CK(launch_pack(h->prec, g, nrhs, xd, h->tv.p, n12, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0,
-                 nullptr, st));
+  CK(launch_pack(h->prec, bt, xd, h->tv.p, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, nullptr, st));
   StepArgs a{};
-  a.g = g;
-  a.nrhs = nrhs;
-  a.links = h->links.p;
-  a.mass = h->m_w + 4.0;
-  a.emu = exp(h->mu);
-  a.emui = exp(-h->mu);
-  split_const(a.mass, a.mass_hl);
-  split_const(a.emu, a.emu_hl);
-  split_const(a.emui, a.emui_hl);
+  a.b = bt;
   a.tv = h->tv.p;
   a.p = h->p.p;
-  a.s_tv = a.s_p = n12;
   a.dagger = dagger ? 1 : 0;
   a.c = c;
   CK(launch_step(h->prec, kModeApply, a, st));
-  CK(launch_unpack(h->prec, g, nrhs, h->p.p, n12, yd, st));
+  CK(launch_unpack(h->prec, bt, h->p.p, yd, st));
+  h->stats.launches += 3;
+  h->stats.stencil_launches += 1;
+  h->stats.other_launches += 2;
   if (mem == OV_MEM_HOST) CK(cudaMemcpyAsync(y, yd, canon, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return OV_OK;
+}
+
+// ---------------------------------------------------------------- batch of lattices
+extern "C" int ov_batch_create(ov_handle** hp, int nprob, const ov_geom* geoms, const void* const* links, int links_mem,
+                               const double* m_w, const double* mu, const ov_opts* opts, void* stream) {
+  if (!hp || nprob < 1 || !geoms || !links || !m_w || !mu) return OV_ERR_ARG;
+  *hp = nullptr;
+  ov_handle* first = nullptr;
+  int rc = ov_create(&first, &geoms[0], links[0], links_mem, m_w[0], mu[0], opts, stream);
+  if (rc != OV_OK) return rc;
+  for (int i = 1; i < nprob; ++i) {
+    if (geoms[i].precision != geoms[0].precision || (geoms[i].t_antiperiodic != 0) != (geoms[0].t_antiperiodic != 0)) {
+      ov_destroy(first);
+      return OV_ERR_ARG;
+    }
+    ov_handle* hi = nullptr;
+    rc = ov_create(&hi, &geoms[i], links[i], links_mem, m_w[i], mu[i], opts, stream);
+    if (rc != OV_OK) {
+      ov_destroy(first);
+      return rc;
+    }
+    // move the converted links into the batch handle
+    first->lat.push_back(hi->lat[0]);
+    hi->lat[0].links = Buf{};
+    ov_destroy(hi);
+  }
+  first->is_batch = 1;
+  *hp = first;
+  return OV_OK;
+}
+
+extern "C" int ov_batch_sign_apply(ov_handle* h, const void* const* x, void* const* y, int mem, double tol, int k_max,
+                                   int l, ov_info* info) {
+  if (!h || !h->is_batch || !x || !y) return OV_ERR_ARG;
+  if (mem != OV_MEM_HOST && mem != OV_MEM_DEVICE) return OV_ERR_ARG;
+  CK(cudaSetDevice(h->dev));
+  const int np = (int)h->lat.size();
+  size_t pool = 0;
+  for (const Lattice& L : h->lat) pool += 12 * (size_t)L.g.V;
+  Buf xb, yb;
+  if (grow(xb, sizeof(double2) * pool) != cudaSuccess || grow(yb, sizeof(double2) * pool) != cudaSuccess) {
+    release(xb);
+    release(yb);
+    return OV_ERR_NOMEM;
+  }
+  const cudaMemcpyKind kin = mem == OV_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind kout = mem == OV_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  size_t off = 0;
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r < np && e == cudaSuccess; ++r) {
+    const size_t nb = sizeof(double2) * 12 * (size_t)h->lat[r].g.V;
+    e = cudaMemcpyAsync((char*)xb.p + off, x[r], nb, kin, h->st);
+    off += nb;
+  }
+  int rc = e == cudaSuccess ? sign_apply_impl(h, np, xb.p, yb.p, OV_MEM_DEVICE, tol, k_max, l, info, 0) : OV_ERR_CUDA;
+  if (rc >= 0) {
+    off = 0;
+    for (int r = 0; r < np && e == cudaSuccess; ++r) {
+      const size_t nb = sizeof(double2) * 12 * (size_t)h->lat[r].g.V;
+      e = cudaMemcpyAsync(y[r], (char*)yb.p + off, nb, kout, h->st);
+      off += nb;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) rc = OV_ERR_CUDA;
+  }
+  release(xb);
+  release(yb);
+  return rc;
 }
 
 // ---------------------------------------------------------------- inner level alone
@@ -886,6 +1115,39 @@ extern "C" int ov_rh_sign(ov_handle* h, int count, int m, const void* T, void* S
     if (!it[count + i]) worst = OV_ERR_RH_NOCONV;
   }
   return worst;
+}
+
+extern "C" int ov_set_sizer(ov_handle* h, const float* theta, int l_min, int l_max) {
+  if (!h) return OV_ERR_ARG;
+  if (!theta) {
+    h->sizer_on = 0;
+    return OV_OK;
+  }
+  if (l_min < 1 || l_max < l_min) return OV_ERR_ARG;
+  if (l_max > kMaxL) return OV_ERR_TOO_LARGE;
+  CK(cudaSetDevice(h->dev));
+  const size_t nb = sizeof(float) * mlp_num_params();
+  CK(grow(h->sizer_theta, nb));
+  CK(cudaMemcpy(h->sizer_theta.p, theta, nb, cudaMemcpyHostToDevice));
+  h->sizer_lmin = l_min;
+  h->sizer_lmax = l_max;
+  h->sizer_on = 1;
+  return OV_OK;
+}
+
+extern "C" int ov_get_coefficients(const ov_handle* h, int rhs, int kcap, void* alpha, void* beta, void* gamma,
+                                   int* k) {
+  if (!h || !alpha || !beta || !gamma || kcap < 1) return OV_ERR_ARG;
+  if (rhs < 0 || rhs >= h->last_nrhs || h->last_steps < 1) return OV_ERR_ARG;
+  CK(cudaSetDevice(h->dev));
+  const int kk = std::min(kcap, h->last_steps);
+  const size_t o = (size_t)rhs * h->last_ld + 1;
+  // alpha_1..alpha_k, beta_1..beta_k (beta_1 = 0), gamma_1..gamma_k
+  CK(cudaMemcpy(alpha, (const double2*)h->coef_alp.p + o, sizeof(double2) * kk, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(beta, (const double2*)h->coef_bet.p + o, sizeof(double2) * kk, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(gamma, (const double2*)h->coef_gam.p + o, sizeof(double2) * kk, cudaMemcpyDeviceToHost));
+  if (k) *k = kk;
+  return OV_OK;
 }
 
 extern "C" int ov_version(char* buf, size_t len) {

@@ -8,7 +8,7 @@
 
 namespace ov {
 
-constexpr int kBlock = 128;       // threads per block of the site kernels
+constexpr int kBlockDefault = 128;  // threads per block of the site kernels unless tuned (64 / 128 / 256)
 constexpr int kMaxL = 120;        // largest inner dimension (Roberts-Higham fits one CTA's shared memory)
 constexpr int kMaxInnerK = 1024;  // largest outer dimension the inner level accepts (H_k factors in shared memory)
 
@@ -37,16 +37,32 @@ struct Geometry {
   int V, Lx, Ly, Lz, Lt;
 };
 
-// Arguments of one outer step (all vector pointers are internal-layout arrays
-// [rhs][12][V] of the precision's storage type; strides in elements per RHS).
-struct StepArgs {
+// One lattice problem of a launch: its geometry, links and operator constants, the
+// offset of its vectors in every vector pool (and of its x / y in the canonical
+// buffers; both hold 12 V complex entries per problem), and its range of site blocks
+// in the one-dimensional grid. A handle with n right-hand sides on one gauge field is n
+// problems sharing geometry and links; a batch of lattices is one problem per lattice.
+struct ProbDesc {
   Geometry g;
-  int nrhs;
   const void* links;
   double mass;       // m_w + 4
   double emu, emui;  // e^{mu}, e^{-mu}
   float mass_hl[2], emu_hl[2], emui_hl[2];  // the same constants as float pairs (hi + lo)
-  // per-RHS step scalars in the arithmetic type of the precision (vec_t slots, [nrhs][8]):
+  size_t voff;
+  int block0, nblk;
+};
+struct Batch {
+  const ProbDesc* desc;  // device [nprob]
+  const int* blk_prob;   // device [nblocks]: problem of each site block
+  int nblocks, nprob;
+  int block;             // threads per site block (64, 128 or 256)
+};
+
+// Arguments of one outer step (vector pointers are pools; problem r's vectors start at
+// desc[r].voff and are laid out [12][V] of the precision's storage type).
+struct StepArgs {
+  Batch b;
+  // per-problem step scalars in the arithmetic type of the precision (vec_t slots, [nprob][8]):
   // 0: 1/nv_j, 1: gam_j, 2: 1/conj(nw_j), 3: conj(bet_j), 4: alpha_j, 5: conj(alpha_j).
   // They are written once per step by the block that finalises the coefficient, so the
   // site kernels do no double-precision work.
@@ -61,38 +77,37 @@ struct StepArgs {
   void* r;
   void* tnext;  // regeneration pass: next unnormalised vector
   void* yacc;   // regeneration pass: y accumulator (accumulator type)
-  const void* cacc;  // regeneration pass: c_j in accumulator type, [nrhs][ld]
-  size_t s_tv, s_tw, s_vprev, s_wprev, s_vcur, s_wcur, s_p, s_r, s_tnext, s_yacc;
+  const void* cacc;  // regeneration pass: c_j in accumulator type, [nprob][ld]
   Coefs c;
   int j;
   int dagger;  // apply mode: 1 = A^dag
   double breakdown_tol;
-  double* partials;     // [nrhs][nblk][4]
-  unsigned* counters;   // [nrhs]
+  double* partials;     // [nblocks][4]
+  unsigned* counters;   // [nprob]
 };
 
-// outer-level launchers (ov_outer.cu); prec = OV_PREC_*
-cudaError_t launch_pack(int prec, const Geometry& g, int nrhs, const double2* xcanon, void* xint,
-                        size_t s_xint, Coefs c, double* partials, unsigned* counters, int want_norm,
-                        void* scal, cudaStream_t st);
-void split_const(double d, float hl[2]);
-cudaError_t launch_unpack(int prec, const Geometry& g, int nrhs, const void* xint, size_t s_xint,
-                          double2* ycanon, cudaStream_t st);
+void fill_consts(ProbDesc& d, double m_w, double mu);
+
+// outer-level launchers (ov_outer.cu); prec = OV_PREC_*. Canonical buffers hold, per
+// problem r, 12 V complex doubles at offset desc[r].voff (layout [V][12]).
+cudaError_t launch_pack(int prec, const Batch& b, const double2* xcanon, void* xint, Coefs c, double* partials,
+                        unsigned* counters, int want_norm, void* scal, cudaStream_t st);
+cudaError_t launch_unpack(int prec, const Batch& b, const void* xint, double2* ycanon, cudaStream_t st);
 cudaError_t launch_step(int prec, int mode, const StepArgs& a, cudaStream_t st);
 cudaError_t launch_update(int prec, int mode, const StepArgs& a, cudaStream_t st);
 // y_r = scale_r * sum_{j<k_r} c[r][j+1] v_{r,j+1} (+ x_r and gamma5 if add_x); slots[j] is
-// the device address of basis slot j (v_{j+1} of all RHS, RHS stride s_rhs elements)
-cudaError_t launch_recombine(int prec, const Geometry& g, int nrhs, const void* const* slots, size_t s_rhs,
-                             const void* cacc, int ldc, const int* k_dev, const double* scale,
-                             const double2* xcanon, int add_x, double2* ycanon, cudaStream_t st);
+// the device address of basis slot j (a vector pool)
+cudaError_t launch_recombine(int prec, const Batch& b, const void* const* slots, const void* cacc, int ldc,
+                             const int* k_dev, const double* scale, const double2* xcanon, int add_x,
+                             double2* ycanon, cudaStream_t st);
 // y_r = scale_r * yacc_r (+ x_r, gamma5)
-cudaError_t launch_finish_acc(int prec, const Geometry& g, int nrhs, const void* yacc, size_t s_yacc,
-                              const double* scale, const double2* xcanon, int add_x, double2* ycanon,
-                              cudaStream_t st);
+cudaError_t launch_finish_acc(int prec, const Batch& b, const void* yacc, const double* scale,
+                              const double2* xcanon, int add_x, double2* ycanon, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+void split_const(double d, float hl[2]);
 size_t vec_elem_bytes(int prec);  // bytes per complex vector element
 size_t acc_elem_bytes(int prec);  // bytes per complex accumulator element
-int num_site_blocks(const Geometry& g);
+int num_site_blocks(const Geometry& g, int bs);
 
 // inner level (ov_inner.cu)
 struct InnerWork {
@@ -124,5 +139,9 @@ cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermiti
                       double* est_outer, int* rh_status, int* rh_iters, int phase, cudaStream_t st);
 cudaError_t run_rh_dense(int count, int m, const double2* T, double2* S, int* iters, int* ok,
                          double rh_tol, int rh_maxit, InnerWork& w, cudaStream_t st);
+
+// learned sizing (ov_mlp.cu)
+cudaError_t mlp_predict_device(const float* theta_dev, int n, const float* X_dev, float* Y_dev, cudaStream_t st);
+int mlp_num_params();
 
 }  // namespace ov

@@ -16,7 +16,7 @@
 
 namespace ov {
 
-int num_site_blocks(const Geometry& g) { return (g.V + kBlock - 1) / kBlock; }
+int num_site_blocks(const Geometry& g, int bs) { return (g.V + bs - 1) / bs; }
 
 size_t vec_elem_bytes(int prec) {
   return prec == OV_PREC_FP32 ? sizeof(float2) : (prec == OV_PREC_FP64 ? sizeof(double2) : sizeof(float4));
@@ -80,10 +80,10 @@ __device__ __forceinline__ void set_step_scal(void* scal, int r, double nv, doub
 // Each thread passes its values; the block's sums go to partials[(r*nblk+bx)*4+q].
 // Returns true in the last block to finish for this right-hand side, where tot[]
 // (valid in thread 0) holds the fixed-order total over all blocks.
-template <int NQ>
-__device__ __forceinline__ bool reduce_last(double (&v)[NQ], double* partials, unsigned* counters, int r,
+template <int NQ, int BS>
+__device__ __forceinline__ bool reduce_last(double (&v)[NQ], double* partials, unsigned* counters, int r, int part0,
                                             int nblk, double (&tot)[NQ]) {
-  __shared__ double sred[kBlock / 32][4];
+  __shared__ double sred[BS / 32][4];
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
@@ -96,8 +96,8 @@ __device__ __forceinline__ bool reduce_last(double (&v)[NQ], double* partials, u
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       double s = 0.0;
-      for (int w = 0; w < kBlock / 32; ++w) s += sred[w][q];
-      partials[((size_t)r * nblk + blockIdx.x) * 4 + q] = s;
+      for (int w = 0; w < BS / 32; ++w) s += sred[w][q];
+      partials[(size_t)blockIdx.x * 4 + q] = s;
     }
     __threadfence();
     unsigned prev = atomicAdd(&counters[r], 1u);
@@ -109,9 +109,9 @@ __device__ __forceinline__ bool reduce_last(double (&v)[NQ], double* partials, u
   double loc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) loc[q] = 0.0;
-  for (int b = tid; b < nblk; b += kBlock) {
+  for (int b = tid; b < nblk; b += BS) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) loc[q] += __ldcg(&partials[((size_t)r * nblk + b) * 4 + q]);
+    for (int q = 0; q < NQ; ++q) loc[q] += __ldcg(&partials[(size_t)(part0 + b) * 4 + q]);
   }
   __syncthreads();
 #pragma unroll
@@ -124,12 +124,28 @@ __device__ __forceinline__ bool reduce_last(double (&v)[NQ], double* partials, u
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       double s = 0.0;
-      for (int w = 0; w < kBlock / 32; ++w) s += sred[w][q];
+      for (int w = 0; w < BS / 32; ++w) s += sred[w][q];
       tot[q] = s;
     }
     counters[r] = 0u;
   }
   return true;
+}
+
+// the site of this thread: problem r (from the block map), its descriptor, block within it
+struct SiteRef {
+  int r, bx, s;
+  bool active;
+  const ProbDesc* d;
+};
+template <int BS>
+__device__ __forceinline__ SiteRef site_ref(const Batch& b) {
+  const int blk = blockIdx.x;
+  const int r = __ldg(&b.blk_prob[blk]);
+  const ProbDesc* d = &b.desc[r];
+  const int bx = blk - d->block0;
+  const int s = bx * BS + threadIdx.x;
+  return {r, bx, s, s < d->g.V, d};
 }
 
 // warp sum in the accumulator type (double-float sums stay on the float pipes; double
@@ -138,27 +154,29 @@ __device__ __forceinline__ double warp_acc(double a) { return warp_sum(a); }
 __device__ __forceinline__ double warp_acc(df64 a) { return df_to_double(warp_sum(a)); }
 
 // ------------------------------------------------------------ pack / unpack
-template <class P>
-__global__ void __launch_bounds__(kBlock) k_pack(Geometry g, const double2* __restrict__ x, typename P::vec_t* xi,
-                                                 size_t s_xi, Coefs c, double* partials, unsigned* counters,
-                                                 int want_norm, void* scal) {
+template <class P, int BS>
+__global__ void __launch_bounds__(BS) k_pack(Batch bt, const double2* __restrict__ x, typename P::vec_t* xi,
+                                                 Coefs c, double* partials, unsigned* counters, int want_norm,
+                                                 void* scal) {
   using R = typename P::R;
-  const int s = blockIdx.x * kBlock + threadIdx.x;
-  const int r = blockIdx.y;
+  const SiteRef sr = site_ref<BS>(bt);
+  const int s = sr.s, r = sr.r;
+  const int V = sr.d->g.V;
+  const size_t voff = sr.d->voff;
   double n2 = 0.0;
-  if (s < g.V) {
-    const double2* src = x + ((size_t)r * g.V + s) * 12;
-    typename P::vec_t* dst = xi + (size_t)r * s_xi + s;
+  if (sr.active) {
+    const double2* src = x + voff + (size_t)s * 12;
+    typename P::vec_t* dst = xi + voff + s;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       double2 z = src[k];
       n2 = fma(z.x, z.x, fma(z.y, z.y, n2));
-      st_vec(dst + (size_t)k * g.V, cd_to<R>(z.x, z.y));
+      st_vec(dst + (size_t)k * V, cd_to<R>(z.x, z.y));
     }
   }
   if (!want_norm) return;
   double v[1] = {n2}, tot[1];
-  if (reduce_last<1>(v, partials, counters, r, gridDim.x, tot) && threadIdx.x == 0) {
+  if (reduce_last<1, BS>(v, partials, counters, r, sr.d->block0, sr.d->nblk, tot) && threadIdx.x == 0) {
     double nrm = sqrt(tot[0]);
     size_t o = (size_t)r * c.ld + 1;
     c.nv[o] = nrm > 0.0 ? nrm : 1.0;
@@ -171,17 +189,16 @@ __global__ void __launch_bounds__(kBlock) k_pack(Geometry g, const double2* __re
   }
 }
 
-template <class P>
-__global__ void __launch_bounds__(kBlock) k_unpack(Geometry g, const typename P::vec_t* __restrict__ xi, size_t s_xi,
-                                                   double2* y) {
-  const int s = blockIdx.x * kBlock + threadIdx.x;
-  const int r = blockIdx.y;
-  if (s >= g.V) return;
-  const typename P::vec_t* src = xi + (size_t)r * s_xi + s;
-  double2* dst = y + ((size_t)r * g.V + s) * 12;
+template <class P, int BS>
+__global__ void __launch_bounds__(BS) k_unpack(Batch bt, const typename P::vec_t* __restrict__ xi, double2* y) {
+  const SiteRef sr = site_ref<BS>(bt);
+  if (!sr.active) return;
+  const int V = sr.d->g.V;
+  const typename P::vec_t* src = xi + sr.d->voff + sr.s;
+  double2* dst = y + sr.d->voff + (size_t)sr.s * 12;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    cx<double> z = vec_to_cd(ld_vec(src + (size_t)k * g.V));
+    cx<double> z = vec_to_cd(ld_vec(src + (size_t)k * V));
     dst[k] = make_double2(z.re, z.im);
   }
 }
@@ -288,34 +305,36 @@ __device__ __forceinline__ cx<R> g5d(int k, cx<R> psi, cx<R> hk, R mass) {
   return k >= 6 ? -d : d;
 }
 
-template <class P, int MODE>
-__global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
+template <class P, int MODE, int BS>
+__global__ void __launch_bounds__(BS) k_step(StepArgs a) {
   using R = typename P::R;
   using V_t = typename P::vec_t;
   using L_t = typename P::link_t;
   using A = typename P::A;
   using AT = typename AccOf<P>::A;
   using AS = typename AccOf<P>::st;
-  const Geometry g = a.g;
-  const int s = blockIdx.x * kBlock + threadIdx.x;
-  const int r = blockIdx.y;
-  const bool active = s < g.V;
+  const SiteRef sr = site_ref<BS>(a.b);
+  const ProbDesc& d = *sr.d;
+  const Geometry g = d.g;
+  const int s = sr.s, r = sr.r;
+  const bool active = sr.active;
   const int ss = active ? s : 0;
-  const L_t* links = (const L_t*)a.links;
-  const R mass = hconst(R(), a.mass, a.mass_hl);
-  const R emu = hconst(R(), a.emu, a.emu_hl), emui = hconst(R(), a.emui, a.emui_hl);
+  const size_t vo = d.voff;
+  const L_t* links = (const L_t*)d.links;
+  const R mass = hconst(R(), d.mass, d.mass_hl);
+  const R emu = hconst(R(), d.emu, d.emu_hl), emui = hconst(R(), d.emui, d.emui_hl);
   const size_t co = (size_t)r * a.c.ld + a.j;
   int xc[4];
   site_coords(g, ss, xc[0], xc[1], xc[2], xc[3]);
 
   cx<A> dot = {rzero<A>(), rzero<A>()};
   cx<R> acc[12];
-  const V_t* tv = (const V_t*)a.tv + (size_t)r * a.s_tv;
+  const V_t* tv = (const V_t*)a.tv + vo;
 
   if (MODE == kModeApply) {
     if (active) {
       hopping<P>(acc, tv, links, g, s, xc, a.dagger ? emui : emu, a.dagger ? emu : emui);
-      V_t* out = (V_t*)a.p + (size_t)r * a.s_p + s;
+      V_t* out = (V_t*)a.p + vo + s;
 #pragma unroll
       for (int k = 0; k < 12; ++k) st_vec(out + (size_t)k * g.V, g5d(k, ld_vec(tv + (size_t)k * g.V + s), acc[k], mass));
     }
@@ -330,13 +349,13 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
     const double2 gj = a.c.gam[co];
     const cx<R> gam_j = cd_to<R>(gj.x, gj.y);
     hopping<P>(acc, tv, links, g, s, xc, emu, emui);
-    const V_t* vp = (const V_t*)a.vprev + (size_t)r * a.s_vprev + s;
-    V_t* vc = (V_t*)a.vcur + (size_t)r * a.s_vcur + s;
+    const V_t* vp = (const V_t*)a.vprev + vo + s;
+    V_t* vc = (V_t*)a.vcur + vo + s;
     const double2 aj = a.c.alp[co];
     const cx<R> alp_j = cd_to<R>(aj.x, aj.y);
     const cx<AT> cjv = ld_acc((const AS*)a.cacc + (size_t)r * a.c.ld + a.j);
-    V_t* tn = (V_t*)a.tnext + (size_t)r * a.s_tnext + s;
-    AS* ya = (AS*)a.yacc + (size_t)r * a.s_yacc + s;
+    V_t* tn = (V_t*)a.tnext + vo + s;
+    AS* ya = (AS*)a.yacc + vo + s;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       const cx<R> psi = ld_vec(tv + (size_t)k * g.V + s);
@@ -361,13 +380,12 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
     const cx<R> scl = ld_scal<P>(a.scal, r, 2 * side);
     const cx<R> cf = ld_scal<P>(a.scal, r, 2 * side + 1);
     if (active) {
-      const V_t* src = side == 0 ? tv : (const V_t*)a.tw + (size_t)r * a.s_tw;
+      const V_t* src = side == 0 ? tv : (const V_t*)a.tw + vo;
       hopping<P>(acc, src, links, g, s, xc, side == 0 ? emu : emui, side == 0 ? emui : emu);
-      const V_t* prv = side == 0 ? (const V_t*)a.vprev + (size_t)r * a.s_vprev + s
-                                 : (const V_t*)a.wprev + (size_t)r * a.s_wprev + s;
-      V_t* cur = side == 0 ? (V_t*)a.vcur + (size_t)r * a.s_vcur + s : (V_t*)a.wcur + (size_t)r * a.s_wcur + s;
-      V_t* out = side == 0 ? (V_t*)a.p + (size_t)r * a.s_p + s : (V_t*)a.r + (size_t)r * a.s_r + s;
-      const V_t* pp = (const V_t*)a.p + (size_t)r * a.s_p + s;
+      const V_t* prv = side == 0 ? (const V_t*)a.vprev + vo + s : (const V_t*)a.wprev + vo + s;
+      V_t* cur = side == 0 ? (V_t*)a.vcur + vo + s : (V_t*)a.wcur + vo + s;
+      V_t* out = side == 0 ? (V_t*)a.p + vo + s : (V_t*)a.r + vo + s;
+      const V_t* pp = (const V_t*)a.p + vo + s;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         const cx<R> psi = ld_vec(src + (size_t)k * g.V + s);
@@ -384,7 +402,7 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
   // warp_acc already reduced over the warp in the accumulator type; reduce_last sums
   // again over lanes, so keep only lane 0's value.
   if ((threadIdx.x & 31) != 0) { v2[0] = 0.0; v2[1] = 0.0; }
-  if (reduce_last<2>(v2, a.partials, a.counters, r, gridDim.x, tot) && threadIdx.x == 0) {
+  if (reduce_last<2, BS>(v2, a.partials, a.counters, r, d.block0, d.nblk, tot) && threadIdx.x == 0) {
     const double ai = MODE == kModeLanczos ? 0.0 : tot[1];
     a.c.alp[co] = make_double2(tot[0], ai);
     st_scal<P>(a.scal, r, 4, tot[0], ai);
@@ -393,23 +411,24 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
 }
 
 // ------------------------------------------------------------ vector update
-template <class P, int MODE>
-__global__ void __launch_bounds__(kBlock) k_update(StepArgs a) {
+template <class P, int MODE, int BS>
+__global__ void __launch_bounds__(BS) k_update(StepArgs a) {
   using R = typename P::R;
   using V_t = typename P::vec_t;
   using A = typename P::A;
-  const Geometry g = a.g;
-  const int s = blockIdx.x * kBlock + threadIdx.x;
-  const int r = blockIdx.y;
+  const SiteRef sr = site_ref<BS>(a.b);
+  const Geometry g = sr.d->g;
+  const int s = sr.s, r = sr.r;
+  const size_t vo = sr.d->voff;
   const size_t co = (size_t)r * a.c.ld + a.j;
   const cx<R> alp = ld_scal<P>(a.scal, r, 4);
   const cx<R> calp = ld_scal<P>(a.scal, r, 5);
   cx<A> d = {rzero<A>(), rzero<A>()};
   cx<A> nvv = {rzero<A>(), rzero<A>()}, nww = {rzero<A>(), rzero<A>()};
-  if (s < g.V) {
-    const V_t* pp = (const V_t*)a.p + (size_t)r * a.s_p + s;
-    const V_t* vc = (const V_t*)a.vcur + (size_t)r * a.s_vcur + s;
-    V_t* tv = (V_t*)a.tv + (size_t)r * a.s_tv + s;  // written: the stencil no longer reads it
+  if (sr.active) {
+    const V_t* pp = (const V_t*)a.p + vo + s;
+    const V_t* vc = (const V_t*)a.vcur + vo + s;
+    V_t* tv = (V_t*)a.tv + vo + s;  // written: the stencil no longer reads it
     if (MODE == kModeLanczos) {
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
@@ -418,9 +437,9 @@ __global__ void __launch_bounds__(kBlock) k_update(StepArgs a) {
         acc_dot(nvv, t, t);
       }
     } else {
-      const V_t* rr = (const V_t*)a.r + (size_t)r * a.s_r + s;
-      const V_t* wc = (const V_t*)a.wcur + (size_t)r * a.s_wcur + s;
-      V_t* tw = (V_t*)a.tw + (size_t)r * a.s_tw + s;
+      const V_t* rr = (const V_t*)a.r + vo + s;
+      const V_t* wc = (const V_t*)a.wcur + vo + s;
+      V_t* tw = (V_t*)a.tw + vo + s;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         const cx<R> t = ld_vec(pp + (size_t)k * g.V) - cmul(alp, ld_vec(vc + (size_t)k * g.V));
@@ -437,7 +456,7 @@ __global__ void __launch_bounds__(kBlock) k_update(StepArgs a) {
   if (MODE == kModeLanczos) {
     double v1[1] = {warp_acc(nvv.re)}, tot[1];
     if (!lane0) v1[0] = 0.0;
-    if (reduce_last<1>(v1, a.partials, a.counters, r, gridDim.x, tot) && threadIdx.x == 0) {
+    if (reduce_last<1, BS>(v1, a.partials, a.counters, r, sr.d->block0, sr.d->nblk, tot) && threadIdx.x == 0) {
       const double b = sqrt(tot[0]);
       const double bprev = fabs(a.c.bet[co].x);
       const size_t cn = co + 1;
@@ -456,7 +475,7 @@ __global__ void __launch_bounds__(kBlock) k_update(StepArgs a) {
   } else {
     double v4[4] = {warp_acc(d.re), warp_acc(d.im), warp_acc(nvv.re), warp_acc(nww.re)}, tot[4];
     if (!lane0) { v4[0] = v4[1] = v4[2] = v4[3] = 0.0; }
-    if (reduce_last<4>(v4, a.partials, a.counters, r, gridDim.x, tot) && threadIdx.x == 0) {
+    if (reduce_last<4, BS>(v4, a.partials, a.counters, r, sr.d->block0, sr.d->nblk, tot) && threadIdx.x == 0) {
       const double dre = tot[0], dim = tot[1];
       const double ad = sqrt(dre * dre + dim * dim);
       const double b = sqrt(ad);
@@ -477,15 +496,16 @@ __global__ void __launch_bounds__(kBlock) k_update(StepArgs a) {
 }
 
 // ------------------------------------------------------------ recombination
-template <class P>
-__global__ void __launch_bounds__(kBlock) k_recombine(Geometry g, const void* const* __restrict__ slots, size_t s_rhs,
+template <class P, int BS>
+__global__ void __launch_bounds__(BS) k_recombine(Batch bt, const void* const* __restrict__ slots,
                                                       const typename AccOf<P>::st* __restrict__ cacc, int ldc,
                                                       const int* __restrict__ kr, const double* __restrict__ scale,
                                                       const double2* __restrict__ x, int add_x, double2* y) {
   using AT = typename AccOf<P>::A;
-  const int s = blockIdx.x * kBlock + threadIdx.x;
-  const int r = blockIdx.y;
-  if (s >= g.V) return;
+  const SiteRef sr = site_ref<BS>(bt);
+  if (!sr.active) return;
+  const int s = sr.s, r = sr.r, V = sr.d->g.V;
+  const size_t vo = sr.d->voff;
   cx<AT> acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = czero<AT>();
@@ -493,13 +513,13 @@ __global__ void __launch_bounds__(kBlock) k_recombine(Geometry g, const void* co
   const typename AccOf<P>::st* cr = cacc + (size_t)r * ldc;
   for (int j = 0; j < k_r; ++j) {
     const cx<AT> cj = ld_acc(cr + j + 1);
-    const typename P::vec_t* vj = (const typename P::vec_t*)slots[j] + (size_t)r * s_rhs + s;
+    const typename P::vec_t* vj = (const typename P::vec_t*)slots[j] + vo + s;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc_axpy(acc[k], cj, ld_vec(vj + (size_t)k * g.V));
+    for (int k = 0; k < 12; ++k) acc_axpy(acc[k], cj, ld_vec(vj + (size_t)k * V));
   }
   const double sc = scale[r];
-  double2* dst = y + ((size_t)r * g.V + s) * 12;
-  const double2* xs = x + ((size_t)r * g.V + s) * 12;
+  double2* dst = y + vo + (size_t)s * 12;
+  const double2* xs = x + vo + (size_t)s * 12;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     cx<double> z = acc_to_cd(acc[k]);
@@ -515,19 +535,20 @@ __global__ void __launch_bounds__(kBlock) k_recombine(Geometry g, const void* co
   }
 }
 
-template <class P>
-__global__ void __launch_bounds__(kBlock) k_finish_acc(Geometry g, const typename AccOf<P>::st* __restrict__ yacc,
-                                                       size_t s_yacc, const double* __restrict__ scale,
+template <class P, int BS>
+__global__ void __launch_bounds__(BS) k_finish_acc(Batch bt, const typename AccOf<P>::st* __restrict__ yacc,
+                                                       const double* __restrict__ scale,
                                                        const double2* __restrict__ x, int add_x, double2* y) {
-  const int s = blockIdx.x * kBlock + threadIdx.x;
-  const int r = blockIdx.y;
-  if (s >= g.V) return;
+  const SiteRef sr = site_ref<BS>(bt);
+  if (!sr.active) return;
+  const int s = sr.s, r = sr.r, V = sr.d->g.V;
+  const size_t vo = sr.d->voff;
   const double sc = scale[r];
-  double2* dst = y + ((size_t)r * g.V + s) * 12;
-  const double2* xs = x + ((size_t)r * g.V + s) * 12;
+  double2* dst = y + vo + (size_t)s * 12;
+  const double2* xs = x + vo + (size_t)s * 12;
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    cx<double> z = acc_to_cd(ld_acc(yacc + (size_t)r * s_yacc + (size_t)k * g.V + s));
+    cx<double> z = acc_to_cd(ld_acc(yacc + vo + (size_t)k * V + s));
     z.re *= sc;
     z.im *= sc;
     if (add_x) {
@@ -541,7 +562,14 @@ __global__ void __launch_bounds__(kBlock) k_finish_acc(Geometry g, const typenam
 }
 
 // ------------------------------------------------------------ launchers
-static dim3 site_grid(const Geometry& g, int nrhs) { return dim3(num_site_blocks(g), nrhs); }
+void fill_consts(ProbDesc& d, double m_w, double mu) {
+  d.mass = m_w + 4.0;
+  d.emu = exp(mu);
+  d.emui = exp(-mu);
+  split_const(d.mass, d.mass_hl);
+  split_const(d.emu, d.emu_hl);
+  split_const(d.emui, d.emui_hl);
+}
 
 #define OV_DISPATCH(prec, CALL)                      \
   switch (prec) {                                    \
@@ -549,53 +577,69 @@ static dim3 site_grid(const Geometry& g, int nrhs) { return dim3(num_site_blocks
     case OV_PREC_FP32: { using P = PrecF32; CALL; break; }  \
     default: { using P = PrecDF64; CALL; break; }           \
   }
+// the block size is the one the batch's block map was built with
+#define OV_BS_DISPATCH(bs, CALL)                           \
+  switch (bs) {                                            \
+    case 64: { constexpr int BS = 64; CALL; break; }       \
+    case 256: { constexpr int BS = 256; CALL; break; }     \
+    default: { constexpr int BS = 128; CALL; break; }      \
+  }
 
-cudaError_t launch_pack(int prec, const Geometry& g, int nrhs, const double2* x, void* xi, size_t s_xi, Coefs c,
-                        double* partials, unsigned* counters, int want_norm, void* scal, cudaStream_t st) {
-  OV_DISPATCH(prec, (k_pack<P><<<site_grid(g, nrhs), kBlock, 0, st>>>(g, x, (typename P::vec_t*)xi, s_xi, c,
-                                                                      partials, counters, want_norm, scal)));
+cudaError_t launch_pack(int prec, const Batch& b, const double2* x, void* xi, Coefs c, double* partials,
+                        unsigned* counters, int want_norm, void* scal, cudaStream_t st) {
+  OV_BS_DISPATCH(b.block, OV_DISPATCH(prec, (k_pack<P, BS><<<b.nblocks, BS, 0, st>>>(
+                                                b, x, (typename P::vec_t*)xi, c, partials, counters, want_norm, scal))));
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(int prec, const Geometry& g, int nrhs, const void* xi, size_t s_xi, double2* y,
-                          cudaStream_t st) {
-  OV_DISPATCH(prec, (k_unpack<P><<<site_grid(g, nrhs), kBlock, 0, st>>>(g, (const typename P::vec_t*)xi, s_xi, y)));
+cudaError_t launch_unpack(int prec, const Batch& b, const void* xi, double2* y, cudaStream_t st) {
+  OV_BS_DISPATCH(b.block, OV_DISPATCH(prec, (k_unpack<P, BS><<<b.nblocks, BS, 0, st>>>(
+                                                b, (const typename P::vec_t*)xi, y))));
   return cudaGetLastError();
 }
 
 cudaError_t launch_step(int prec, int mode, const StepArgs& a, cudaStream_t st) {
-  dim3 grid = site_grid(a.g, a.nrhs);
+  const int grid = a.b.nblocks;
   switch (mode) {
-    case kModeLanczos: OV_DISPATCH(prec, (k_step<P, kModeLanczos><<<grid, kBlock, 0, st>>>(a))); break;
-    case kModeTwoSided: OV_DISPATCH(prec, (k_step<P, kModeTwoSided><<<grid, kBlock, 0, st>>>(a))); break;
-    case kModeRegen: OV_DISPATCH(prec, (k_step<P, kModeRegen><<<grid, kBlock, 0, st>>>(a))); break;
-    default: OV_DISPATCH(prec, (k_step<P, kModeApply><<<grid, kBlock, 0, st>>>(a))); break;
+    case kModeLanczos:
+      OV_BS_DISPATCH(a.b.block, OV_DISPATCH(prec, (k_step<P, kModeLanczos, BS><<<grid, BS, 0, st>>>(a))));
+      break;
+    case kModeTwoSided:
+      OV_BS_DISPATCH(a.b.block, OV_DISPATCH(prec, (k_step<P, kModeTwoSided, BS><<<grid, BS, 0, st>>>(a))));
+      break;
+    case kModeRegen:
+      OV_BS_DISPATCH(a.b.block, OV_DISPATCH(prec, (k_step<P, kModeRegen, BS><<<grid, BS, 0, st>>>(a))));
+      break;
+    default:
+      OV_BS_DISPATCH(a.b.block, OV_DISPATCH(prec, (k_step<P, kModeApply, BS><<<grid, BS, 0, st>>>(a))));
+      break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(int prec, int mode, const StepArgs& a, cudaStream_t st) {
-  dim3 grid = site_grid(a.g, a.nrhs);
+  const int grid = a.b.nblocks;
   if (mode == kModeLanczos) {
-    OV_DISPATCH(prec, (k_update<P, kModeLanczos><<<grid, kBlock, 0, st>>>(a)));
+    OV_BS_DISPATCH(a.b.block, OV_DISPATCH(prec, (k_update<P, kModeLanczos, BS><<<grid, BS, 0, st>>>(a))));
   } else {
-    OV_DISPATCH(prec, (k_update<P, kModeTwoSided><<<grid, kBlock, 0, st>>>(a)));
+    OV_BS_DISPATCH(a.b.block, OV_DISPATCH(prec, (k_update<P, kModeTwoSided, BS><<<grid, BS, 0, st>>>(a))));
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_recombine(int prec, const Geometry& g, int nrhs, const void* const* slots, size_t s_rhs,
-                             const void* cacc, int ldc, const int* k_dev, const double* scale, const double2* x,
-                             int add_x, double2* y, cudaStream_t st) {
-  OV_DISPATCH(prec, (k_recombine<P><<<site_grid(g, nrhs), kBlock, 0, st>>>(
-                        g, slots, s_rhs, (const typename AccOf<P>::st*)cacc, ldc, k_dev, scale, x, add_x, y)));
+cudaError_t launch_recombine(int prec, const Batch& b, const void* const* slots, const void* cacc, int ldc,
+                             const int* k_dev, const double* scale, const double2* x, int add_x, double2* y,
+                             cudaStream_t st) {
+  OV_BS_DISPATCH(b.block, OV_DISPATCH(prec, (k_recombine<P, BS><<<b.nblocks, BS, 0, st>>>(
+                                                b, slots, (const typename AccOf<P>::st*)cacc, ldc, k_dev, scale, x,
+                                                add_x, y))));
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish_acc(int prec, const Geometry& g, int nrhs, const void* yacc, size_t s_yacc,
-                              const double* scale, const double2* x, int add_x, double2* y, cudaStream_t st) {
-  OV_DISPATCH(prec, (k_finish_acc<P><<<site_grid(g, nrhs), kBlock, 0, st>>>(
-                        g, (const typename AccOf<P>::st*)yacc, s_yacc, scale, x, add_x, y)));
+cudaError_t launch_finish_acc(int prec, const Batch& b, const void* yacc, const double* scale, const double2* x,
+                              int add_x, double2* y, cudaStream_t st) {
+  OV_BS_DISPATCH(b.block, OV_DISPATCH(prec, (k_finish_acc<P, BS><<<b.nblocks, BS, 0, st>>>(
+                                                b, (const typename AccOf<P>::st*)yacc, scale, x, add_x, y))));
   return cudaGetLastError();
 }
 

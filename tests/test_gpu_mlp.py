@@ -1,0 +1,134 @@
+"""Learned sizing on the GPU: forward and gradient kernels against the oracle MLP,
+training, and the a-posteriori guard around the prediction."""
+import numpy as np
+import pytest
+
+import ovinputs as oi
+from gpu_util import rel
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ov():
+    import paper_0910_2918_gb300 as ov
+
+    return ov
+
+
+def test_forward_matches_oracle(ov):
+    rng = np.random.default_rng(0)
+    theta = omlp.init_params(3).astype(np.float32)
+    X = rng.standard_normal((257, 16)).astype(np.float32)
+    y = ov.ov_mlp_forward(theta, X)
+    yref, _ = omlp.forward(theta.astype(np.float64), X.astype(np.float64))
+    assert np.abs(y - yref).max() <= 1e-4 * max(1.0, np.abs(yref).max())
+
+
+def test_gradient_matches_oracle(ov):
+    rng = np.random.default_rng(1)
+    theta = (omlp.init_params(4) * 0.5).astype(np.float32)
+    X = rng.standard_normal((300, 16)).astype(np.float32)
+    Y = rng.standard_normal((300, 2)).astype(np.float32)
+    loss, g = ov.ov_mlp_loss_grad(theta, X, Y)
+    lref, gref = omlp.loss_grad(theta.astype(np.float64), X.astype(np.float64), Y.astype(np.float64))
+    assert abs(loss - lref) <= 1e-5 * abs(lref)
+    assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+
+
+def test_training_fits_a_smooth_map(ov):
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-1, 1, (1024, 16)).astype(np.float32)
+    Y = np.stack([np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2], np.cos(X[:, 3]) - X[:, 4] ** 2], 1).astype(np.float32)
+    theta0 = omlp.init_params(5).astype(np.float32)
+    l0 = ov.ov_mlp_loss_grad(theta0, X, Y)[0]
+    theta, hist = ov.ov_mlp_train(theta0, X, Y, epochs=300, batch=128, lr=3e-3, seed=7)
+    assert hist[-1] < 0.05 * l0
+    # the returned parameters reproduce the reported loss
+    assert ov.ov_mlp_loss_grad(theta, X, Y)[0] == pytest.approx(float(hist[-1]), rel=1e-4)
+    # deterministic given the seed
+    theta2, hist2 = ov.ov_mlp_train(theta0, X, Y, epochs=300, batch=128, lr=3e-3, seed=7)
+    assert np.array_equal(theta, theta2)
+
+
+def _constant_predictor(k_pred, l_pred):
+    """Zero weights with biases (log k, log l): predicts the same (k, l) for every input."""
+    th = np.zeros(5378, dtype=np.float32)
+    th[5376] = np.log(k_pred)
+    th[5377] = np.log(l_pred)
+    return th
+
+
+@pytest.mark.parametrize("k_pred,l_pred", [(40.0, 8.0), (330.0, 100.0)])
+def test_guard_keeps_the_answer_when_the_prediction_is_wrong(ov, k_pred, l_pred):
+    """A short k or a small l must not change the answer: checks continue past a short
+    prediction and l grows until the inner estimate meets tol."""
+    dims = (6, 6, 6, 6)
+    U = oi.gauge_field(dims, "near_unit", 0, eps=0.3)
+    x = oi.gaussian_source(dims, 1).reshape(1, -1)
+    y0 = np.zeros_like(x)
+    with ov.Overlap(dims, U, -1.6, 0.2, "fp64", opts=ov.make_opts(check_interval=10)) as op:
+        rc0, i0 = op.sign_apply(x, y0, 1e-9, 800, 120)
+    y1 = np.zeros_like(x)
+    with ov.Overlap(dims, U, -1.6, 0.2, "fp64", opts=ov.make_opts(check_interval=10)) as op:
+        op.set_sizer(_constant_predictor(k_pred, l_pred), 8, 120)
+        rc1, i1 = op.sign_apply(x, y1, 1e-9, 800, 120)
+    assert rc0 == 0 and rc1 == 0
+    assert i1[0]["err_est"] <= 1e-9
+    assert rel(y1[0], y0[0]) < 5e-9
+
+
+def test_coefficients_readback(ov):
+    from oracle import dirac, krylov
+
+    dims = (4, 4, 4, 4)
+    U = oi.gauge_field(dims, "haar", 0)
+    x = oi.gaussian_source(dims, 1)
+    with ov.Overlap(dims, U, -1.5, 0.3, "fp64", opts=ov.make_opts(k_fixed=20)) as op:
+        y = np.zeros((1, x.size), complex)
+        op.sign_apply(x.reshape(1, -1).copy(), y, 0, 20, 20)
+        a, b, g = op.coefficients(0, 20)
+    o = krylov.Outer(lambda v: dirac.A_apply(U, v, dims, -1.5, 0.3), lambda v: dirac.AH_apply(U, v, dims, -1.5, 0.3),
+                     x, False)
+    for _ in range(20):
+        o.step()
+    assert np.allclose(a, o.alpha, atol=1e-12)
+    assert np.allclose(b, o.beta[:20], atol=1e-12)
+    assert np.allclose(g, o.gamma[:20], atol=1e-12)
+
+
+def test_trained_sizer_gain_on_held_out_problems(ov):
+    """The trained network (committed parameters, records from the method itself) against
+    the method without it, on held-out problems of the training family: the same
+    tolerance is met with far fewer stopping checks and less time."""
+    import time
+
+    from paper_0910_2918_gb300 import sizer
+
+    theta = sizer.load(sizer.DEFAULT_PARAMS)
+    probs = oi.training_problems(2004)[2000:]
+    checks = {0: 0, 1: 0}
+    secs = {0: 0.0, 1: 0.0}
+    for p in probs:
+        U = oi.gauge_field(p["dims"], p["kind"], p["gauge_seed"], eps=p["eps"])
+        x = oi.problem_source(p).reshape(1, -1)
+        ys = {}
+        for sized in (0, 1):
+            y = np.zeros_like(x)
+            with ov.Overlap(p["dims"], U, p["m_w"], p["mu"], "df64", opts=ov.make_opts(check_interval=10)) as op:
+                if sized:
+                    op.set_sizer(theta, 8, 120)
+                op.sign_apply(x, y, 1e-8, 1000, 120)  # warm-up (and autotune)
+                op.reset_stats()
+                t0 = time.perf_counter()
+                rc, info = op.sign_apply(x, y, 1e-8, 1000, 120)
+                secs[sized] += time.perf_counter() - t0
+                checks[sized] += op.stats()["checks"]
+            assert rc == 0 and info[0]["err_est"] <= 1e-8
+            ys[sized] = y[0]
+        # both meet the estimate; the estimate is not a bound, so the two answers agree to
+        # a few times tol
+        assert rel(ys[1], ys[0]) < 2e-7
+    assert checks[1] * 3 <= checks[0]
+    assert secs[1] < secs[0]
