@@ -36,6 +36,11 @@ METRIC = "sgn(γ5D_w)x applies/s at 16^4, μ=0.2, rel.err≤1e-8; stencil % of H
 DIMS = (16, 16, 16, 16)
 MU, M_W, EPS = 0.2, -1.6, 0.3
 TOL, K_MAX, L_INNER = 1e-8, 1000, 72
+# the a-posteriori estimate is not a bound (it undershoots the true error by up to ~3x on
+# this workload), so the run stops at a tighter estimate and every apply is then checked
+# against the double-precision path: only applies with a measured error <= TOL count
+TOL_STOP = 2e-9
+L_MAX = 120
 NRHS = 12
 PREC = "df64"
 CHECK_FIRST, CHECK_EVERY = 100, 25
@@ -45,9 +50,10 @@ PROFILE = os.path.join(ROOT, "profiles", "stencil_twosided_df64_16x16x16x16_12rh
 
 def workload_desc():
     return (f"{DIMS[0]}^4 lattice, near-unit links eps={EPS} (seed 0), mu={MU}, m_w={M_W}, "
-            f"{NRHS} spin-colour point sources at site 0, tol {TOL:g}, k<={K_MAX}, l={L_INNER}, "
-            f"first check at the learned k* (else k={CHECK_FIRST}), then every >={CHECK_EVERY} steps "
-            f"(adaptive schedule), l from the learned l* (<= {L_INNER}), double-float vectors / float links")
+            f"{NRHS} spin-colour point sources at site 0, rel.err <= {TOL:g} measured against the FP64 "
+            f"path (stopping estimate {TOL_STOP:g}), k<={K_MAX}, l={L_INNER}, "
+            f"first check at the learned k* (else k={CHECK_FIRST}), then every {CHECK_EVERY} steps, "
+            f"l from the learned l* (<= {L_INNER}), double-float vectors / float links")
 
 
 def make_inputs():
@@ -187,14 +193,15 @@ def run_ours(args, rank, world, local_rank):
     U, X = make_inputs()
     n = X.shape[1]
     stream = torch.cuda.Stream()
-    opts = ov.make_opts(check_interval=CHECK_EVERY, first_check=CHECK_FIRST, check_schedule=1, timing=1)
+    # checks: the learned first check, then every CHECK_EVERY steps (fixed schedule)
+    opts = ov.make_opts(check_interval=CHECK_EVERY, first_check=CHECK_FIRST, check_schedule=0, timing=1)
     op = ov.Overlap(DIMS, U, M_W, MU, PREC, opts=opts, stream=stream.cuda_stream)
     # learned sizing: the committed network predicts the first check and l after 16 steps
     sized = not args.no_sizer
     if sized:
         from paper_0910_2918_gb300 import sizer
 
-        op.set_sizer(sizer.load(sizer.DEFAULT_PARAMS), 8, L_INNER)
+        op.set_sizer(sizer.load(sizer.DEFAULT_PARAMS), 8, L_MAX)
     xd = torch.from_numpy(X).cuda()
     yd = torch.zeros_like(xd)
     xh = torch.from_numpy(X).pin_memory()
@@ -205,7 +212,7 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     for _ in range(args.warmup):
-        rc, info = op.sign_apply(xd, yd, TOL, K_MAX, L_INNER)
+        rc, info = op.sign_apply(xd, yd, TOL_STOP, K_MAX, L_INNER)
     torch.cuda.synchronize()
     # timed region: device-resident inputs
     op.reset_stats()
@@ -213,12 +220,10 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    good = 0
     with Clocks(local_rank) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            rc, info = op.sign_apply(xd, yd, TOL, K_MAX, L_INNER)
-            good += sum(1 for i in info if i["status"] == 0 and i["err_est"] <= TOL)
+            rc, info = op.sign_apply(xd, yd, TOL_STOP, K_MAX, L_INNER)
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
@@ -228,20 +233,15 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    good_e2e = 0
     for _ in range(args.steps):
-        rc, info_e = op.sign_apply(xh.numpy(), yh.numpy(), TOL, K_MAX, L_INNER)
-        good_e2e += sum(1 for i in info_e if i["status"] == 0 and i["err_est"] <= TOL)
+        rc, info_e = op.sign_apply(xh.numpy(), yh.numpy(), TOL_STOP, K_MAX, L_INNER)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     barrier()
     tmax = torch.tensor([ms, t_e2e * 1e3], dtype=torch.float64, device="cuda")
-    gsum = torch.tensor([good, good_e2e], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(gsum, op=dist.ReduceOp.SUM)
     ms_max, e2e_ms = float(tmax[0]), float(tmax[1])
-    good_all, good_e2e_all = float(gsum[0]), float(gsum[1])
     # the float (mixed-precision) stencil on the same workload: HBM fraction of its fused
     # two-sided step (k fixed, outside the timed region)
     fp32_stencil = None
@@ -269,27 +269,38 @@ def run_ours(args, rank, world, local_rank):
         with ov.Overlap(DIMS, U, M_W, MU, "fp64", opts=ov.make_opts(check_interval=10),
                         stream=stream.cuda_stream) as opp:
             yp = torch.zeros((1, n), dtype=torch.complex128, device="cuda")
-            opp.sign_apply(xd[0:1].contiguous(), yp, TOL, K_MAX, L_INNER)  # warm-up
+            opp.sign_apply(xd[0:1].contiguous(), yp, TOL_STOP, K_MAX, L_INNER)  # warm-up
             for r in sel:
                 torch.cuda.synchronize()
                 ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 ea.record(stream)
-                opp.sign_apply(xd[r:r + 1].contiguous(), yp, TOL, K_MAX, L_INNER)
+                opp.sign_apply(xd[r:r + 1].contiguous(), yp, TOL_STOP, K_MAX, L_INNER)
                 eb.record(stream)
                 torch.cuda.synchronize()
                 t_plain += ea.elapsed_time(eb)
         plain = {"applies_per_s": len(sel) / (t_plain * 1e-3), "sample": f"RHS {sel} one at a time",
                  "form": "FP64 vectors, one RHS per call, checks every 10 steps, l=%d, no sizing" % L_INNER}
-    # accuracy against the double-precision path (outside the timed region, rank 0)
-    err_fp64 = None
-    if rank == 0 and not args.no_validate:
+    # accuracy of every apply against the double-precision path (outside the timed region):
+    # the same 12 sources with FP64 vectors and links, stopped at 1e-10
+    errs = None
+    if not args.no_validate:
         with ov.Overlap(DIMS, U, M_W, MU, "fp64", opts=ov.make_opts(check_interval=CHECK_EVERY,
-                                                                    first_check=CHECK_FIRST)) as ref:
-            sel = [0, 7]
-            yr = torch.zeros((len(sel), n), dtype=torch.complex128, device="cuda")
-            ref.sign_apply(xd[sel].contiguous(), yr, 1e-10, K_MAX, 100)
-            err_fp64 = max(float(torch.linalg.norm(yd[s] - yr[i]) / torch.linalg.norm(yr[i]))
-                           for i, s in enumerate(sel))
+                                                                    first_check=CHECK_FIRST, check_schedule=1),
+                        stream=stream.cuda_stream) as ref:
+            yr = torch.zeros_like(xd)
+            ref.sign_apply(xd, yr, 1e-10, K_MAX, 120)
+            errs = [float(torch.linalg.norm(yd[r] - yr[r]) / torch.linalg.norm(yr[r])) for r in range(NRHS)]
+            errs_e2e = [float(torch.linalg.norm(yh[r].cuda() - yr[r]) / torch.linalg.norm(yr[r]))
+                        for r in range(NRHS)]
+        good = args.steps * sum(1 for e in errs if e <= TOL)
+        good_e2e = args.steps * sum(1 for e in errs_e2e if e <= TOL)
+    else:
+        good = args.steps * sum(1 for i in info if i["status"] == 0 and i["err_est"] <= TOL)
+        good_e2e = good
+    gsum = torch.tensor([good, good_e2e], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(gsum, op=dist.ReduceOp.SUM)
+    good_all, good_e2e_all = float(gsum[0]), float(gsum[1])
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -332,7 +343,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": workload_desc(), "global_batch": NRHS * world, "parallelism": f"replicas{world}",
                    "learned_sizing": sized,
                    "l2": "working set per step >> L2 (12 x k x 12.6 MB stored basis)", "k_used": k_used,
-                   "l_used": l_used, "applies_within_tol": good_frac, "rel_err_vs_fp64_path": err_fp64},
+                   "l_used": l_used, "stop_tol": TOL_STOP, "applies_within_tol": good_frac,
+                   "rel_err_vs_fp64_path_max": max(errs) if errs else None},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "kernel": "k_step<PrecDF64, two-sided> (fused A, A^dag stencil + recurrence)",
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": st_ms, "peak_source": peak_src,
@@ -364,8 +376,8 @@ def run_profile(args):
     import paper_0910_2918_gb300 as ov
 
     U, X = make_inputs()
-    opts = ov.make_opts(k_fixed=args.profile_steps, recombination=0)
-    with ov.Overlap(DIMS, U, M_W, MU, PREC, opts=opts) as op:
+    opts = ov.make_opts(k_fixed=args.profile_steps, recombination=0, block_size=256, graph_steps=0)
+    with ov.Overlap(DIMS, U, M_W, MU, args.profile_prec, opts=opts) as op:
         xd = torch.from_numpy(X).cuda()
         yd = torch.zeros_like(xd)
         rc, info = op.sign_apply(xd, yd, TOL, K_MAX, min(L_INNER, args.profile_steps))
@@ -420,6 +432,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 nested-method comparison")
     ap.add_argument("--no-sizer", action="store_true", help="run without the learned sizing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-prec", default=PREC, choices=["df64", "fp32", "fp64"],
+                    help="arithmetic of the profiling run")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling run: one batched apply of the bench workload with exactly this many "
                          "outer steps (no timing, baseline or validation); for ncu captures")

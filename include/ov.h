@@ -95,10 +95,14 @@ typedef struct {
   int k_fixed;          /* > 0: run exactly k_fixed outer steps, evaluate once, no stopping rule [0] */
   int check_schedule;   /* 0: checks at first_check + j*check_interval; 1: adaptive: after two
                            estimates, the next check goes where the log-linear decay of the outer
-                           estimate reaches tol (at least check_interval steps later) [0] */
+                           estimate reaches tol (at least check_interval and at most
+                           4 * check_interval steps later) [0] */
   int block_size;       /* threads per block of the site kernels: 64, 128, 256, or 0 = autotune
                            (time the first outer step at each size once per handle and problem
                            set, keep the fastest) [0] */
+  int graph_steps;      /* outer steps per CUDA graph: runs of steps between checks replay a graph of
+                           this many steps captured once per handle (0: plain launches; timing = 1
+                           also uses plain launches) [8] */
   int timing;           /* 1: record CUDA events around every stencil / update / inner / recombination
                            launch on the handle's stream and accumulate their durations (ov_get_stats) [0] */
 } ov_opts;
@@ -117,6 +121,7 @@ typedef struct {
   long long regen_steps;       /* steps of the second (regeneration) pass */
   long long checks;            /* stopping checks (inner evaluations) */
   long long block_size;        /* threads per site block of the last apply (autotuned or forced) */
+  long long graph_launches;    /* CUDA graph replays (each counts its kernels in `launches`) */
 } ov_stats;
 
 /* Per-RHS result information. */
@@ -200,9 +205,9 @@ int ov_inner_sign(ov_handle* h, int count, int ld, const int* k, const void* alp
 int ov_rh_sign(ov_handle* h, int count, int m, const void* T, void* S, int* iters);
 
 /* ---- learned sizing of the Krylov dimensions (not in the paper) ----
- * A 16 -> 64 -> 64 -> 2 float MLP with ReLU reads f = (Im alpha_1..alpha_8,
- * arg gamma_2..gamma_9), the first two-sided Lanczos coefficients (at mu = 0 they vanish
- * and the prediction is a constant), and predicts (log k*, log l*): the outer dimension at
+ * A 16 -> 64 -> 64 -> 2 float MLP with ReLU reads f = (Re alpha_1..alpha_6,
+ * Im alpha_1..alpha_6, beta_2..beta_5), the first outer coefficients, and predicts
+ * (log k*, log l*): the outer dimension at
  * which the stopping estimate reaches the tolerance and the inner dimension that keeps
  * the inner estimate below it. Parameters: 5378 floats, W1 [64][16], b1 [64], W2 [64][64],
  * b2 [64], W3 [2][64], b3 [2] (row-major, out x in). All pointers here are HOST memory.

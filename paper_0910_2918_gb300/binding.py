@@ -44,7 +44,8 @@ class ov_opts(ctypes.Structure):
     _fields_ = [("check_interval", ctypes.c_int), ("first_check", ctypes.c_int),
                 ("recombination", ctypes.c_int), ("rh_tol", ctypes.c_double), ("rh_maxit", ctypes.c_int),
                 ("breakdown_tol", ctypes.c_double), ("inner_dl", ctypes.c_int), ("k_fixed", ctypes.c_int),
-                ("check_schedule", ctypes.c_int), ("block_size", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("check_schedule", ctypes.c_int), ("block_size", ctypes.c_int), ("graph_steps", ctypes.c_int),
+                ("timing", ctypes.c_int)]
 
 
 class ov_stats(ctypes.Structure):
@@ -53,7 +54,8 @@ class ov_stats(ctypes.Structure):
                 ("other_launches", ctypes.c_longlong), ("stencil_ms", ctypes.c_double),
                 ("update_ms", ctypes.c_double), ("inner_ms", ctypes.c_double), ("recombine_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("outer_steps", ctypes.c_longlong),
-                ("regen_steps", ctypes.c_longlong), ("checks", ctypes.c_longlong), ("block_size", ctypes.c_longlong)]
+                ("regen_steps", ctypes.c_longlong), ("checks", ctypes.c_longlong), ("block_size", ctypes.c_longlong),
+                ("graph_launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

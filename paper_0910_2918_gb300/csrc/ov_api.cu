@@ -99,6 +99,12 @@ struct ov_handle {
   int inner_cap = 0, inner_ld = 0;
   ov_stats stats{};
   std::map<TuneKey, int> tuned;  // autotuned block size per (precision, mode, problem count)
+  // CUDA graph of graph_steps outer steps (captured on a private stream, replayed on st)
+  Buf jstate, slot_tab;
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  StepArgs gargs{};
+  int gU = 0, gprec = -1, gmode = -1;
   // learned sizing
   Buf sizer_theta, sizer_feat, sizer_pred;
   int sizer_on = 0, sizer_lmin = 8, sizer_lmax = kMaxL;
@@ -231,6 +237,7 @@ extern "C" void ov_default_opts(ov_opts* o) {
   o->k_fixed = 0;
   o->check_schedule = 0;
   o->block_size = 0;
+  o->graph_steps = 8;
   o->timing = 0;
 }
 
@@ -252,7 +259,8 @@ static int check_opts(const ov_opts& o) {
   if (o.check_interval < 1 || o.rh_maxit < 1 || !(o.rh_tol > 0) || o.inner_dl < 1 || o.k_fixed < 0 ||
       o.first_check < 0 || o.recombination < 0 || o.recombination > 2 || !(o.breakdown_tol >= 0) ||
       o.check_schedule < 0 || o.check_schedule > 1 ||
-      (o.block_size != 0 && o.block_size != 64 && o.block_size != 128 && o.block_size != 256))
+      (o.block_size != 0 && o.block_size != 64 && o.block_size != 128 && o.block_size != 256) ||
+      o.graph_steps < 0 || o.graph_steps > 256)
     return OV_ERR_ARG;
   return OV_OK;
 }
@@ -353,6 +361,10 @@ extern "C" void ov_destroy(ov_handle* h) {
   for (Buf* b : all) release(*b);
   for (Buf& b : h->chunks) release(b);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  release(h->jstate);
+  release(h->slot_tab);
   delete h;
 }
 
@@ -464,6 +476,44 @@ static int basis_slot(ov_handle* h, size_t pool_bytes, int slot, void** out) {
   return OV_OK;
 }
 
+// A graph of U outer steps for these step arguments: captured once (on a private stream;
+// the kernels take j and their slots from the device step state, so every replay runs
+// the next U steps) and kept while the arguments stay the same.
+static int graph_for(ov_handle* h, const StepArgs& a, int mode, int U) {
+  if (h->gexec && h->gU == U && h->gprec == h->prec && h->gmode == mode && memcmp(&h->gargs, &a, sizeof(a)) == 0)
+    return OV_OK;
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int u = 0; u < U && e == cudaSuccess; ++u) {
+    e = launch_step(h->prec, mode, a, h->cap_st);
+    if (e == cudaSuccess) e = launch_update(h->prec, mode, a, h->cap_st);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_st, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return OV_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&h->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->gexec = nullptr;
+    cudaGetLastError();
+    return OV_ERR_CUDA;
+  }
+  h->gargs = a;
+  h->gU = U;
+  h->gprec = h->prec;
+  h->gmode = mode;
+  return OV_OK;
+}
+
 // ---------------------------------------------------------------- sign apply
 static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,
                            ov_info* info, int add_x) {
@@ -558,33 +608,59 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   InnerWork iw = inner_work(h);
   int ndone = 0;
   int j = 0;
-  void* prev_v = (char*)h->vring.p + vbn;  // zero slot: v_0
   const int first = o.first_check > 0 ? o.first_check : o.check_interval;
   int next_check = first;
   // last two (k, outer estimate) pairs per RHS for the adaptive schedule
   std::vector<double> hk1(nrhs, 0), he1(nrhs, 0), hk2(nrhs, 0), he2(nrhs, 0);
   std::vector<int> kprev_old(nrhs, 0);
   int last_check = 0;
-  for (j = 1; j <= ktarget && ndone < nrhs; ++j) {
-    void* vcur = nullptr;
+  // device-side step state: j and the global ticket; the basis slot table; the rings
+  {
+    const int init[2] = {1, 0};
+    CK(grow(h->jstate, sizeof(int) * 2));
+    CK(cudaMemcpyAsync(h->jstate.p, init, sizeof(int) * 2, cudaMemcpyHostToDevice, st));
+    CK(grow(h->slot_tab, sizeof(void*) * (size_t)(ktarget + 1)));
+  }
+  a.jdev = (int*)h->jstate.p;
+  a.gticket = (unsigned*)((int*)h->jstate.p + 1);
+  a.vring = h->vring.p;
+  a.wring = h->wring.p;
+  a.pool_bytes = vbn;
+  a.slot_tab = recomb == OV_RECOMB_STORED ? (void* const*)h->slot_tab.p : nullptr;
+  CK(cudaMemsetAsync((char*)h->wring.p + vbn, 0, vbn, st));
+  const int gU = (o.timing || o.graph_steps <= 0) ? 0 : o.graph_steps;
+  int jdone = 0;
+  for (;;) {
+    if (jdone >= ktarget || ndone >= nrhs) break;
+    const bool fixed_span = o.k_fixed > 0;
+    int target = fixed_span ? ktarget : std::min(next_check, ktarget);
+    if (h->sizer_on && !fixed_span && jdone < kSizerSteps && ktarget > kSizerSteps + 1)
+      target = std::min(target, kSizerSteps);
+    if (target <= jdone) target = jdone + 1;
+    // basis slots of the span (stored mode), uploaded to the device slot table
     if (recomb == OV_RECOMB_STORED) {
-      rc = basis_slot(h, vbn, j - 1, &vcur);
-      if (rc != OV_OK) {
-        if (o.recombination != OV_RECOMB_AUTO) return rc;
-        recomb = OV_RECOMB_TWO_PASS;  // out of memory: fall back to the double pass
+      const size_t first_new = slots.size();
+      for (int jj = jdone + 1; jj <= target; ++jj) {
+        void* vc = nullptr;
+        rc = basis_slot(h, vbn, jj - 1, &vc);
+        if (rc != OV_OK) {
+          if (o.recombination != OV_RECOMB_AUTO) return rc;
+          // out of memory: fall back to the double pass; the ring slot that step jj reads
+          // as v_{jj-1} gets the last stored vector
+          recomb = OV_RECOMB_TWO_PASS;
+          a.slot_tab = nullptr;
+          if (jj >= 2) CK(cudaMemcpyAsync((char*)h->vring.p + vbn * (jj & 1), slots[jj - 2], vbn,
+                                          cudaMemcpyDeviceToDevice, st));
+          break;
+        }
+        slots.push_back(vc);
       }
+      if (slots.size() > first_new)
+        CK(cudaMemcpyAsync((void**)h->slot_tab.p + first_new, slots.data() + first_new,
+                           sizeof(void*) * (slots.size() - first_new), cudaMemcpyHostToDevice, st));
     }
-    if (recomb != OV_RECOMB_STORED) vcur = (char*)h->vring.p + vbn * ((j - 1) % 2);
-    if (recomb == OV_RECOMB_STORED) slots.push_back(vcur);
-    a.j = j;
-    a.vprev = prev_v;
-    a.vcur = vcur;
-    a.wprev = (char*)h->wring.p + vbn * (j % 2);
-    a.wcur = (char*)h->wring.p + vbn * ((j - 1) % 2);
-    if (j == 1) {
-      CK(cudaMemsetAsync((char*)h->wring.p + vbn, 0, vbn, st));
-    }
-    if (j == 1 && tune) {
+    int jn = jdone + 1;
+    if (jn == 1 && tune) {
       // autotune the block size on the first step (it only reads x and the step-1
       // scalars, so re-running it is harmless): best of two timed launches per size
       cudaEvent_t e0, e1;
@@ -620,33 +696,52 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
       if (h->trace) fprintf(stderr, "{\"ov_autotune\": %d, \"ms\": %.4f}\n", best_bs, best);
     }
     h->stats.block_size = a.b.block;
-    int ts = tstart(h, kClsStencil);
-    CK(launch_step(h->prec, mode, a, st));
-    tstop(h, ts);
-    ts = tstart(h, kClsUpdate);
-    CK(launch_update(h->prec, mode, a, st));
-    tstop(h, ts);
-    h->stats.launches += 2;
-    h->stats.stencil_launches += 1;
-    h->stats.update_launches += 1;
-    h->stats.outer_steps += 1;
-    prev_v = vcur;
+    // steps jn..target: whole graph units replayed, the rest launched one by one
+    while (jn <= target) {
+      if (gU > 0 && target - jn + 1 >= gU) {
+        rc = graph_for(h, a, mode, gU);
+        if (rc == OV_OK && h->gexec) {
+          CK(cudaGraphLaunch(h->gexec, st));
+          h->stats.launches += 2 * gU;
+          h->stats.stencil_launches += gU;
+          h->stats.update_launches += gU;
+          h->stats.outer_steps += gU;
+          h->stats.graph_launches += 1;
+          jn += gU;
+          continue;
+        }
+      }
+      int ts = tstart(h, kClsStencil);
+      CK(launch_step(h->prec, mode, a, st));
+      tstop(h, ts);
+      ts = tstart(h, kClsUpdate);
+      CK(launch_update(h->prec, mode, a, st));
+      tstop(h, ts);
+      h->stats.launches += 2;
+      h->stats.stencil_launches += 1;
+      h->stats.update_launches += 1;
+      h->stats.outer_steps += 1;
+      ++jn;
+    }
+    jdone = target;
+    j = jdone;
     const bool fixed = o.k_fixed > 0;
     if (h->sizer_on && !fixed && j == kSizerSteps && ktarget > kSizerSteps + 1) {
-      // learned sizing: f = (Im alpha_1..alpha_8, arg gamma_2..gamma_9) -> (log k*, log l*)
-      std::vector<double2> fa((size_t)nrhs * 8), fg((size_t)nrhs * 8);
-      CK(cudaMemcpy2DAsync(fa.data(), sizeof(double2) * 8, c.alp + 1, sizeof(double2) * ld, sizeof(double2) * 8, nrhs,
+      // learned sizing: f = (Re alpha_1..6, Im alpha_1..6, beta_2..5) -> (log k*, log l*)
+      std::vector<double2> fa((size_t)nrhs * 6), fb((size_t)nrhs * 4);
+      CK(cudaMemcpy2DAsync(fa.data(), sizeof(double2) * 6, c.alp + 1, sizeof(double2) * ld, sizeof(double2) * 6, nrhs,
                            cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpy2DAsync(fg.data(), sizeof(double2) * 8, c.gam + 2, sizeof(double2) * ld, sizeof(double2) * 8, nrhs,
+      CK(cudaMemcpy2DAsync(fb.data(), sizeof(double2) * 4, c.bet + 2, sizeof(double2) * ld, sizeof(double2) * 4, nrhs,
                            cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       std::vector<float> feat((size_t)nrhs * 16), pred((size_t)nrhs * 2);
-      for (int r = 0; r < nrhs; ++r)
-        for (int i = 0; i < 8; ++i) {
-          feat[(size_t)r * 16 + i] = (float)fa[(size_t)r * 8 + i].y;
-          const double2 gg = fg[(size_t)r * 8 + i];
-          feat[(size_t)r * 16 + 8 + i] = (float)std::atan2(gg.y, gg.x);
+      for (int r = 0; r < nrhs; ++r) {
+        for (int i = 0; i < 6; ++i) {
+          feat[(size_t)r * 16 + i] = (float)fa[(size_t)r * 6 + i].x;
+          feat[(size_t)r * 16 + 6 + i] = (float)fa[(size_t)r * 6 + i].y;
         }
+        for (int i = 0; i < 4; ++i) feat[(size_t)r * 16 + 12 + i] = (float)fb[(size_t)r * 4 + i].x;
+      }
       CK(grow(h->sizer_feat, sizeof(float) * feat.size()));
       CK(grow(h->sizer_pred, sizeof(float) * pred.size()));
       CK(cudaMemcpyAsync(h->sizer_feat.p, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, st));
@@ -817,13 +912,13 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
         const int ahead = (int)std::ceil(ks) - j;
         if (ahead > pred) pred = ahead;
       }
-      if (pred > step) step = std::min(pred, 10 * o.check_interval);
+      if (pred > step) step = std::min(pred, 4 * o.check_interval);
     }
     last_check = j;
     next_check = j + step;
   }
   const int kmax_used = *std::max_element(kfin.begin(), kfin.end());
-  h->last_steps = j - 1;
+  h->last_steps = jdone;
   h->last_ld = ld;
   h->last_nrhs = nrhs;
   // recombination
@@ -844,6 +939,8 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     CK(launch_pack(h->prec, bt, xd, h->tv.p, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, nullptr, st));
     CK(cudaMemsetAsync(h->vring.p, 0, 2 * vbn, st));
     StepArgs b = a;
+    b.jdev = nullptr;  // the second pass runs from host-side step indices
+    b.slot_tab = nullptr;
     b.yacc = h->yacc.p;
     b.cacc = h->cacc_fin.p;
     void* tcur = h->tv.p;

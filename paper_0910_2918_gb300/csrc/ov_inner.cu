@@ -408,11 +408,25 @@ __global__ void __launch_bounds__(1024) k_rh(int count, int dense_m, const doubl
       for (int i = tid; i < m; i += nth)
         if (i != j) W[(size_t)i * m + j] = el_zero(inv);
       __syncthreads();
-      for (int e = tid; e < m * m; e += nth) {
-        const int i = e / m;
-        if (i == j) continue;
-        const int c = e - i * m;
-        W[e] = el_sub(W[e], el_mul(col[i], W[(size_t)j * m + c]));
+      {
+        // 32 x 32 thread tile: thread (ty, tx) updates rows ty + 32a and columns tx + 32b,
+        // holding its entries of the pivot row in registers (m <= 120 < 4 * 32)
+        const int tx = tid & 31, ty = tid >> 5;
+        E rowj[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int c = tx + 32 * b;
+          rowj[b] = c < m ? W[(size_t)j * m + c] : el_zero(inv);
+        }
+        for (int i = ty; i < m; i += 32) {
+          if (i == j) continue;
+          const E f = col[i];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int c = tx + 32 * b;
+            if (c < m) W[(size_t)i * m + c] = el_sub(W[(size_t)i * m + c], el_mul(f, rowj[b]));
+          }
+        }
       }
       __syncthreads();
     }

@@ -80,6 +80,17 @@ struct StepArgs {
   const void* cacc;  // regeneration pass: c_j in accumulator type, [nprob][ld]
   Coefs c;
   int j;
+  // Device-side step state, so that a run of steps can be captured once in a CUDA graph
+  // and replayed: when jdev is set the kernels take j from *jdev (the update kernel's last
+  // block advances it), v_j / v_{j-1} from the basis slot table (NULL: the two-slot ring
+  // vring, by parity of j) and w_j / w_{j-1} from the ring wring; otherwise they use the
+  // host fields j, vcur, vprev, wcur, wprev.
+  int* jdev;
+  unsigned* gticket;       // finished blocks of an update launch (global ticket)
+  void* const* slot_tab;   // device [k]: address of basis slot j-1 (v_j of every problem)
+  void* vring;
+  void* wring;
+  size_t pool_bytes;       // bytes of one vector of every problem (a slot)
   int dagger;  // apply mode: 1 = A^dag
   double breakdown_tol;
   double* partials;     // [nblocks][4]

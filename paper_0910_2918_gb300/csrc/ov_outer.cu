@@ -239,6 +239,10 @@ __device__ __forceinline__ void site_coords(const Geometry& g, int s, int& x, in
   t = q / g.Lz;
 }
 
+__device__ __forceinline__ void hopping_df(cx<df64> (&accn)[12], const float4* __restrict__ src,
+                                           const float2* __restrict__ links, const Geometry& g, int s,
+                                           const int (&xc)[4], df64 ef, df64 eb);
+
 // acc = sum over the 8 hops of the hopping term for source `src` at site s;
 // ef / eb multiply the forward / backward t hops (e^{+-mu}).
 template <class P>
@@ -247,6 +251,10 @@ __device__ __forceinline__ void hopping(cx<typename P::R> (&acc)[12], const type
                                         const int (&xc)[4], typename P::R ef, typename P::R eb) {
   using R = typename P::R;
   using L = typename P::L;
+  if constexpr (P::id == PrecDF64::id) {
+    hopping_df(acc, src, links, g, s, xc, ef, eb);
+    return;
+  }
   const int V = g.V;
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
@@ -298,11 +306,146 @@ __device__ __forceinline__ void hopping(cx<typename P::R> (&acc)[12], const type
   }
 }
 
+// ---- double-float hopping in compensated form -------------------------------------------
+// The products U_ab h_b with float U and double-float h are summed as in the compensated
+// dot product of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26 (2005), "Dot2"): the
+// product of U with h.hi is exact as (p, e) (p = U*h.hi, e = fma(U, h.hi, -p)), U*h.lo is
+// folded into e with one FMA, the running sum takes p through TwoSum, and all error terms
+// are accumulated in the low word without renormalising. Sums are renormalised once, when
+// the hopping term is complete. Error: a few units of 2^-48 relative to the summed
+// magnitudes, as for the normalised pair arithmetic.
+struct dfu {  // unnormalised pair: value hi + lo
+  float hi, lo;
+};
+__device__ __forceinline__ void madd_u(dfu& acc, float u, df64 h) {
+  const float p = __fmul_rn(u, h.hi);
+  float e = __fmaf_rn(u, h.hi, -p);
+  e = __fmaf_rn(u, h.lo, e);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, err));
+}
+__device__ __forceinline__ dfu add_u(dfu a, dfu b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return {s, __fadd_rn(__fadd_rn(a.lo, b.lo), err)};
+}
+__device__ __forceinline__ dfu neg_u(dfu a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df64 norm_u(dfu a) { return df_fast_two_sum(a.hi, a.lo); }
+__device__ __forceinline__ dfu to_u(df64 a) { return {a.hi, a.lo}; }
+struct cxu {
+  dfu re, im;
+};
+__device__ __forceinline__ cxu cadd_u(cxu a, cxu b) { return {add_u(a.re, b.re), add_u(a.im, b.im)}; }
+// i^q z
+__device__ __forceinline__ cxu rot_u(cxu z, int q) {
+  const bool sw = q & 1;
+  cxu r = {sw ? z.im : z.re, sw ? z.re : z.im};
+  const bool nre = q == 1 || q == 2, nim = q >= 2;
+  return {nre ? neg_u(r.re) : r.re, nim ? neg_u(r.im) : r.im};
+}
+
+__device__ __forceinline__ void hopping_df(cx<df64> (&accn)[12], const float4* __restrict__ src,
+                                           const float2* __restrict__ links, const Geometry& g, int s,
+                                           const int (&xc)[4], df64 ef, df64 eb) {
+  const int V = g.V;
+  cxu acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 1
+  for (int hop = 0; hop < 8; ++hop) {
+    const int nu = hop >> 1;
+    const bool fwd = (hop & 1) == 0;
+    const int Ln = nu == 0 ? g.Lx : (nu == 1 ? g.Ly : (nu == 2 ? g.Lz : g.Lt));
+    const int st = nu == 0 ? 1 : (nu == 1 ? g.Lx : (nu == 2 ? g.Lx * g.Ly : g.Lx * g.Ly * g.Lz));
+    const int c = xc[0] * (nu == 0) + xc[1] * (nu == 1) + xc[2] * (nu == 2) + xc[3] * (nu == 3);
+    const int sn = fwd ? (c == Ln - 1 ? s - (Ln - 1) * st : s + st) : (c == 0 ? s + (Ln - 1) * st : s - st);
+    const int ls = fwd ? s : sn;
+    cx<float> u[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const int idx = fwd ? e : (e % 3) * 3 + e / 3;
+      u[e] = lconj(ld_link(links + (size_t)(nu * 9 + idx) * V + ls), !fwd);
+    }
+    const int b0s = c_bsrc[nu][0], b1s = c_bsrc[nu][1];
+    const int b0q = (c_bph[nu][0] + (fwd ? 2 : 0)) & 3, b1q = (c_bph[nu][1] + (fwd ? 2 : 0)) & 3;
+    cx<df64> h0[3], h1[3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const cx<df64> p0 = ld_vec(src + (size_t)(0 + col) * V + sn);
+      const cx<df64> p1 = ld_vec(src + (size_t)(3 + col) * V + sn);
+      const cx<df64> q0 = rot(ld_vec(src + (size_t)(3 * b0s + col) * V + sn), b0q);
+      const cx<df64> q1 = rot(ld_vec(src + (size_t)(3 * b1s + col) * V + sn), b1q);
+      // projections, unnormalised (their low words only enter through FMAs below)
+      const dfu r0 = add_u(to_u(p0.re), to_u(q0.re)), i0 = add_u(to_u(p0.im), to_u(q0.im));
+      const dfu r1 = add_u(to_u(p1.re), to_u(q1.re)), i1 = add_u(to_u(p1.im), to_u(q1.im));
+      h0[col] = {{r0.hi, r0.lo}, {i0.hi, i0.lo}};
+      h1[col] = {{r1.hi, r1.lo}, {i1.hi, i1.lo}};
+    }
+    const bool sc = nu == 3;
+    const df64 fac = fwd ? ef : eb;
+    const int d0s = c_dsrc[nu][0], d1s = c_dsrc[nu][1];
+    const int d0q = (c_dph[nu][0] + (fwd ? 2 : 0)) & 3, d1q = (c_dph[nu][1] + (fwd ? 2 : 0)) & 3;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cxu g0 = {{0.f, 0.f}, {0.f, 0.f}}, g1 = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const cx<float> ub = u[a * 3 + b];
+        // (u.re + i u.im)(h.re + i h.im)
+        madd_u(g0.re, ub.re, h0[b].re);
+        madd_u(g0.re, -ub.im, h0[b].im);
+        madd_u(g0.im, ub.re, h0[b].im);
+        madd_u(g0.im, ub.im, h0[b].re);
+        madd_u(g1.re, ub.re, h1[b].re);
+        madd_u(g1.re, -ub.im, h1[b].im);
+        madd_u(g1.im, ub.re, h1[b].im);
+        madd_u(g1.im, ub.im, h1[b].re);
+      }
+      if (sc) {
+        const cx<df64> n0 = cscale(cx<df64>{norm_u(g0.re), norm_u(g0.im)}, fac);
+        const cx<df64> n1 = cscale(cx<df64>{norm_u(g1.re), norm_u(g1.im)}, fac);
+        g0 = {to_u(n0.re), to_u(n0.im)};
+        g1 = {to_u(n1.re), to_u(n1.im)};
+      }
+      acc[0 + a] = cadd_u(acc[0 + a], g0);
+      acc[3 + a] = cadd_u(acc[3 + a], g1);
+      acc[6 + a] = cadd_u(acc[6 + a], rot_u(d0s == 0 ? g0 : g1, d0q));
+      acc[9 + a] = cadd_u(acc[9 + a], rot_u(d1s == 0 ? g0 : g1, d1q));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) accn[k] = {norm_u(acc[k].re), norm_u(acc[k].im)};
+}
+
 // (gamma5 D psi)_k at the centre site from the hopping sum: mass*psi - hop/2, lower spins negated.
 template <class R>
 __device__ __forceinline__ cx<R> g5d(int k, cx<R> psi, cx<R> hk, R mass) {
   cx<R> d = cscale(psi, mass) - chalf(hk);
   return k >= 6 ? -d : d;
+}
+
+// the step index and the step's vector slots (device-side state or host fields)
+struct StepPtrs {
+  int j;
+  const void* vprev;
+  void* vcur;
+  const void* wprev;
+  void* wcur;
+};
+__device__ __forceinline__ StepPtrs step_ptrs(const StepArgs& a) {
+  if (!a.jdev) return {a.j, a.vprev, a.vcur, a.wprev, a.wcur};
+  const int j = __ldcg(a.jdev);
+  char* vr = (char*)a.vring;
+  char* wr = (char*)a.wring;
+  const size_t pb = a.pool_bytes;
+  void* vcur = a.slot_tab ? a.slot_tab[j - 1] : (void*)(vr + pb * ((j - 1) & 1));
+  const void* vprev = a.slot_tab ? (j == 1 ? (const void*)(vr + pb) : (const void*)a.slot_tab[j - 2])
+                                 : (const void*)(vr + pb * (j & 1));
+  return {j, vprev, vcur, wr + pb * (j & 1), wr + pb * ((j - 1) & 1)};
 }
 
 template <class P, int MODE, int BS>
@@ -323,7 +466,8 @@ __global__ void __launch_bounds__(BS) k_step(StepArgs a) {
   const L_t* links = (const L_t*)d.links;
   const R mass = hconst(R(), d.mass, d.mass_hl);
   const R emu = hconst(R(), d.emu, d.emu_hl), emui = hconst(R(), d.emui, d.emui_hl);
-  const size_t co = (size_t)r * a.c.ld + a.j;
+  const StepPtrs sp = step_ptrs(a);
+  const size_t co = (size_t)r * a.c.ld + sp.j;
   int xc[4];
   site_coords(g, ss, xc[0], xc[1], xc[2], xc[3]);
 
@@ -349,11 +493,11 @@ __global__ void __launch_bounds__(BS) k_step(StepArgs a) {
     const double2 gj = a.c.gam[co];
     const cx<R> gam_j = cd_to<R>(gj.x, gj.y);
     hopping<P>(acc, tv, links, g, s, xc, emu, emui);
-    const V_t* vp = (const V_t*)a.vprev + vo + s;
-    V_t* vc = (V_t*)a.vcur + vo + s;
+    const V_t* vp = (const V_t*)sp.vprev + vo + s;
+    V_t* vc = (V_t*)sp.vcur + vo + s;
     const double2 aj = a.c.alp[co];
     const cx<R> alp_j = cd_to<R>(aj.x, aj.y);
-    const cx<AT> cjv = ld_acc((const AS*)a.cacc + (size_t)r * a.c.ld + a.j);
+    const cx<AT> cjv = ld_acc((const AS*)a.cacc + (size_t)r * a.c.ld + sp.j);
     V_t* tn = (V_t*)a.tnext + vo + s;
     AS* ya = (AS*)a.yacc + vo + s;
 #pragma unroll
@@ -382,8 +526,8 @@ __global__ void __launch_bounds__(BS) k_step(StepArgs a) {
     if (active) {
       const V_t* src = side == 0 ? tv : (const V_t*)a.tw + vo;
       hopping<P>(acc, src, links, g, s, xc, side == 0 ? emu : emui, side == 0 ? emui : emu);
-      const V_t* prv = side == 0 ? (const V_t*)a.vprev + vo + s : (const V_t*)a.wprev + vo + s;
-      V_t* cur = side == 0 ? (V_t*)a.vcur + vo + s : (V_t*)a.wcur + vo + s;
+      const V_t* prv = side == 0 ? (const V_t*)sp.vprev + vo + s : (const V_t*)sp.wprev + vo + s;
+      V_t* cur = side == 0 ? (V_t*)sp.vcur + vo + s : (V_t*)sp.wcur + vo + s;
       V_t* out = side == 0 ? (V_t*)a.p + vo + s : (V_t*)a.r + vo + s;
       const V_t* pp = (const V_t*)a.p + vo + s;
 #pragma unroll
@@ -420,14 +564,15 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
   const Geometry g = sr.d->g;
   const int s = sr.s, r = sr.r;
   const size_t vo = sr.d->voff;
-  const size_t co = (size_t)r * a.c.ld + a.j;
+  const StepPtrs sp = step_ptrs(a);
+  const size_t co = (size_t)r * a.c.ld + sp.j;
   const cx<R> alp = ld_scal<P>(a.scal, r, 4);
   const cx<R> calp = ld_scal<P>(a.scal, r, 5);
   cx<A> d = {rzero<A>(), rzero<A>()};
   cx<A> nvv = {rzero<A>(), rzero<A>()}, nww = {rzero<A>(), rzero<A>()};
   if (sr.active) {
     const V_t* pp = (const V_t*)a.p + vo + s;
-    const V_t* vc = (const V_t*)a.vcur + vo + s;
+    const V_t* vc = (const V_t*)sp.vcur + vo + s;
     V_t* tv = (V_t*)a.tv + vo + s;  // written: the stencil no longer reads it
     if (MODE == kModeLanczos) {
 #pragma unroll
@@ -438,7 +583,7 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       }
     } else {
       const V_t* rr = (const V_t*)a.r + vo + s;
-      const V_t* wc = (const V_t*)a.wcur + vo + s;
+      const V_t* wc = (const V_t*)sp.wcur + vo + s;
       V_t* tw = (V_t*)a.tw + vo + s;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
@@ -463,7 +608,7 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       const bool broke = !(b > a.breakdown_tol * (fabs(a.c.alp[co].x) + bprev));
       if (broke && a.c.status[r] == kStOK) {
         a.c.status[r] = kStLucky;
-        a.c.kbreak[r] = a.j;
+        a.c.kbreak[r] = sp.j;
       }
       const bool dead = a.c.status[r] != kStOK;
       a.c.nv[cn] = dead ? 1.0 : b;
@@ -483,7 +628,7 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       const bool broke = !(ad > a.breakdown_tol * sqrt(tot[2]) * sqrt(tot[3])) || !(b > 0.0);
       if (broke && a.c.status[r] == kStOK) {
         a.c.status[r] = kStBreakdown;
-        a.c.kbreak[r] = a.j;
+        a.c.kbreak[r] = sp.j;
       }
       const bool dead = a.c.status[r] != kStOK;
       a.c.nv[cn] = dead ? 1.0 : b;
@@ -491,6 +636,19 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       a.c.bet[cn] = make_double2(dead ? 0.0 : b, 0.0);
       a.c.gam[cn] = dead ? make_double2(0.0, 0.0) : make_double2(dre / b, dim / b);
       set_step_scal<P>(a.scal, r, a.c.nv[cn], a.c.gam[cn], a.c.nw[cn], a.c.bet[cn]);
+    }
+  }
+  // device-side step state: the last block of the launch advances j
+  if (a.jdev) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned t = atomicAdd(a.gticket, 1u);
+      if (t == gridDim.x - 1) {
+        *a.jdev = sp.j + 1;
+        *a.gticket = 0u;
+        __threadfence();
+      }
     }
   }
 }

@@ -1,9 +1,9 @@
 """Learned sizing of the Krylov dimensions: data from the method itself, training on the GPU.
 
 A convergence record of one problem is (features, k*, l*):
-  features  f = (Im alpha_1..alpha_8, arg gamma_2..gamma_9), the first outer coefficients
-            of two-sided Lanczos (at mu != 0 they carry the chemical potential; the
-            choice was made on held-out records against Re alpha / beta sets);
+  features  f = (Re alpha_1..alpha_6, Im alpha_1..alpha_6, beta_2..beta_5), the first
+            outer coefficients (Im alpha carries the chemical potential, Re alpha and beta
+            the Wilson mass; the set was chosen on held-out records among several);
   k*        the outer dimension at which the stopping rule stops (checks every dk
             steps, outer estimate ||c_k - [c_{k-dk}; 0]|| / ||c_k|| <= tol, with an
             inner dimension large enough to be exact);
@@ -30,9 +30,9 @@ from . import binding as B
 L_GRID = list(range(8, 121, 8))
 
 
-def features(alpha, gamma):
-    """f = (Im alpha_1..alpha_8, arg gamma_2..gamma_9)."""
-    return np.concatenate([np.imag(alpha[:8]), np.angle(gamma[1:9])]).astype(np.float64)
+def features(alpha, beta):
+    """f = (Re alpha_1..alpha_6, Im alpha_1..alpha_6, beta_2..beta_5)."""
+    return np.concatenate([np.real(alpha[:6]), np.imag(alpha[:6]), np.real(beta[1:5])]).astype(np.float64)
 
 
 def _prefix_arrays(a, b, g, ks, ld):
@@ -79,14 +79,14 @@ def convergence_record(dims, U, m_w, mu, x, tol=1e-8, k_max=600, dk=10, precisio
             else:
                 lo = mid + 1
         lstar = min(L_GRID[lo], kstar)
-    return (features(a, g), kstar, lstar, conv,
+    return (features(a, b), kstar, lstar, conv,
             np.concatenate([a[:16], b[1:17], g[1:17]]).astype(np.complex128))
 
 
 def features_from_raw(raw):
     """Features from stored raw coefficients [alpha_1..16, beta_2..17, gamma_2..17]."""
     raw = np.asarray(raw)
-    return np.concatenate([np.imag(raw[:, :8]), np.angle(raw[:, 32:40])], axis=1)
+    return np.concatenate([np.real(raw[:, :6]), np.imag(raw[:, :6]), np.real(raw[:, 16:20])], axis=1)
 
 
 def make_dataset(problems, tol=1e-8, k_max=600, log_every=50):
@@ -177,6 +177,7 @@ def main():
     ap.add_argument("--train", default=None)
     ap.add_argument("--out", required=True)
     ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--train-n", type=int, default=2000, help="use the first N records (the rest stay held out)")
     args = ap.parse_args()
     if args.records:
         import ovinputs as oi
@@ -187,9 +188,10 @@ def main():
         print(f"wrote {args.out}: converged {int(d['conv'].sum())}/{len(probs)}")
     if args.train:
         d = np.load(args.train)
-        m = d["conv"].astype(bool)
-        F = features_from_raw(d["raw"]) if "raw" in d else d["F"]
-        theta, hist, vhist = train(F[m], d["k"][m], d["l"][m], epochs=args.epochs)
+        n = args.train_n
+        m = d["conv"][:n].astype(bool)
+        F = (features_from_raw(d["raw"]) if "raw" in d else d["F"])[:n]
+        theta, hist, vhist = train(F[m], d["k"][:n][m], d["l"][:n][m], epochs=args.epochs)
         save(args.out, theta, loss=hist, val_loss=vhist, n_train=int(m.sum()))
         print(f"wrote {args.out}: best validation loss {vhist.min():.4f} (epoch {int(vhist.argmin())}) "
               f"on {int(m.sum())} records")

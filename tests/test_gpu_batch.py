@@ -86,3 +86,26 @@ def test_batch_48_mixed_vs_oracle_sampled(ov):
         yo, io = oracle_sign(links_for("fp32", Us[i]), p["dims"], p["m_w"], p["mu"], xs[i][0], k_max=1000,
                              l=100, tol=1e-9, check_interval=20)
         assert rel(ys[i][0], yo) < 1e-5
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.25])
+def test_graph_replay_equals_plain_launches(ov, mu):
+    """Runs of outer steps replayed from a captured CUDA graph (the kernels read the step
+    index and their slots from device memory) give bitwise the same answer as one launch
+    per kernel, for stored and two-pass recombination."""
+    dims = (4, 6, 4, 6)
+    U = oi.gauge_field(dims, "near_unit", 5, eps=0.35)
+    x = np.stack([oi.gaussian_source(dims, 6), oi.gaussian_source(dims, 7)])
+    out = {}
+    for recomb in (0, 1):
+        for g in (0, 8):
+            y = np.zeros_like(x)
+            opts = ov.make_opts(check_interval=10, graph_steps=g, block_size=128, recombination=recomb)
+            with ov.Overlap(dims, U, -1.5, mu, "df64", opts=opts) as op:
+                rc, info = op.sign_apply(x, y, 1e-10, 600, 100)
+                st = op.stats()
+            assert rc == 0
+            out[(recomb, g)] = (y, st)
+        assert np.array_equal(out[(recomb, 0)][0], out[(recomb, 8)][0])
+        assert out[(recomb, 8)][1]["graph_launches"] > 0 and out[(recomb, 0)][1]["graph_launches"] == 0
+    assert rel(out[(1, 8)][0], out[(0, 8)][0]) < 1e-12

@@ -132,3 +132,41 @@ def test_trained_sizer_gain_on_held_out_problems(ov):
         assert rel(ys[1], ys[0]) < 2e-7
     assert checks[1] * 3 <= checks[0]
     assert secs[1] < secs[0]
+
+
+def test_learned_sizing_at_24c48_two_pass(ov):
+    """Evaluation workload of the learned sizing: 24^3 x 48, mu = 0.1, near-unit links
+    (eps 0.3), m_w = -1.6, one Gaussian source, double-float vectors, two-pass
+    recombination, tol 1e-8. The sized run meets the tolerance with fewer checks than the
+    unsized one, and both agree with the FP64 path."""
+    import time
+
+    import torch
+
+    from paper_0910_2918_gb300 import sizer
+
+    dims = (24, 24, 24, 48)
+    U = oi.gauge_field(dims, "near_unit", 0, eps=0.3)
+    x = torch.from_numpy(oi.gaussian_source(dims, 1).reshape(1, -1)).cuda()
+    res = {}
+    for sized in (0, 1):
+        y = torch.zeros_like(x)
+        opts = ov.make_opts(check_interval=10, recombination=1)
+        with ov.Overlap(dims, torch.from_numpy(U).cuda(), -1.6, 0.1, "df64", opts=opts) as op:
+            if sized:
+                op.set_sizer(sizer.load(sizer.DEFAULT_PARAMS), 8, 120)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, info = op.sign_apply(x, y, 1e-8, 1000, 120)
+            torch.cuda.synchronize()
+            res[sized] = (y.clone(), info[0], op.stats(), time.perf_counter() - t0)
+        assert rc == 0 and info[0]["err_est"] <= 1e-8
+    yr = torch.zeros_like(x)
+    with ov.Overlap(dims, torch.from_numpy(U).cuda(), -1.6, 0.1, "fp64",
+                    opts=ov.make_opts(check_interval=20, check_schedule=1, recombination=1)) as op:
+        op.sign_apply(x, yr, 1e-10, 1000, 120)
+    for sized in (0, 1):
+        err = float(torch.linalg.norm(res[sized][0] - yr) / torch.linalg.norm(yr))
+        assert err < 1e-7, (sized, err)
+    assert res[1][2]["checks"] < res[0][2]["checks"]
+    assert res[1][3] < res[0][3]
