@@ -4,8 +4,9 @@
 Workload (one "step" = one whole batched apply: outer Krylov steps, inner levels,
 Roberts-Higham, recombination): 16^4 lattice, near-unit SU(3) links exp(i 0.3 H)
 (seed 0), mu = 0.2, m_w = -1.6, the 12 spin-colour point sources at site 0,
-stopping tolerance 1e-8, k <= 1000, l = 72, double-float vectors on the float pipes
-with float links. An apply counts when its a-posteriori estimate is <= 1e-8.
+k <= 1000, double-float vectors and links on the float pipes. The run stops on the
+a-posteriori estimate at a tighter tolerance; an apply counts only when its error against
+the FP64 path (measured outside the timed region on all right-hand sides) is <= 1e-8.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,7 +40,7 @@ TOL, K_MAX, L_INNER = 1e-8, 1000, 72
 # the a-posteriori estimate is not a bound (it undershoots the true error by up to ~3x on
 # this workload), so the run stops at a tighter estimate and every apply is then checked
 # against the double-precision path: only applies with a measured error <= TOL count
-TOL_STOP = 2e-9
+TOL_STOP = 5e-9
 L_MAX = 120
 NRHS = 12
 PREC = "df64"
@@ -51,9 +52,10 @@ PROFILE = os.path.join(ROOT, "profiles", "stencil_twosided_df64_16x16x16x16_12rh
 def workload_desc():
     return (f"{DIMS[0]}^4 lattice, near-unit links eps={EPS} (seed 0), mu={MU}, m_w={M_W}, "
             f"{NRHS} spin-colour point sources at site 0, rel.err <= {TOL:g} measured against the FP64 "
-            f"path (stopping estimate {TOL_STOP:g}), k<={K_MAX}, l={L_INNER}, "
+            f"path (stopping estimate {TOL_STOP:g}), k<={K_MAX}, l={L_INNER} before sizing, "
             f"first check at the learned k* (else k={CHECK_FIRST}), then every {CHECK_EVERY} steps, "
-            f"l from the learned l* (<= {L_INNER}), double-float vectors / float links")
+            f"l from the learned l* (grown up to {L_MAX} while the inner estimate is above the stop), "
+            f"double-float vectors and links")
 
 
 def make_inputs():
@@ -266,7 +268,8 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_plain:
         sel = [0, 7]
         t_plain, err_plain = 0.0, 0.0
-        with ov.Overlap(DIMS, U, M_W, MU, "fp64", opts=ov.make_opts(check_interval=10),
+        with ov.Overlap(DIMS, U, M_W, MU, "fp64", opts=ov.make_opts(check_interval=10,
+                                                                    inner_arith=ov.binding.OV_INNER_FP64),
                         stream=stream.cuda_stream) as opp:
             yp = torch.zeros((1, n), dtype=torch.complex128, device="cuda")
             opp.sign_apply(xd[0:1].contiguous(), yp, TOL_STOP, K_MAX, L_INNER)  # warm-up
@@ -279,13 +282,15 @@ def run_ours(args, rank, world, local_rank):
                 torch.cuda.synchronize()
                 t_plain += ea.elapsed_time(eb)
         plain = {"applies_per_s": len(sel) / (t_plain * 1e-3), "sample": f"RHS {sel} one at a time",
-                 "form": "FP64 vectors, one RHS per call, checks every 10 steps, l=%d, no sizing" % L_INNER}
+                 "form": "FP64 vectors and inner level, one RHS per call, checks every 10 steps, l=%d, "
+                         "no sizing" % L_INNER}
     # accuracy of every apply against the double-precision path (outside the timed region):
     # the same 12 sources with FP64 vectors and links, stopped at 1e-10
     errs = None
     if not args.no_validate:
         with ov.Overlap(DIMS, U, M_W, MU, "fp64", opts=ov.make_opts(check_interval=CHECK_EVERY,
-                                                                    first_check=CHECK_FIRST, check_schedule=1),
+                                                                    first_check=CHECK_FIRST, check_schedule=1,
+                                                                    inner_arith=ov.binding.OV_INNER_FP64),
                         stream=stream.cuda_stream) as ref:
             yr = torch.zeros_like(xd)
             ref.sign_apply(xd, yr, 1e-10, K_MAX, 120)
@@ -314,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
     hbm = hbm or 6800.0
     # dominant kernel: the fused two-sided stencil step; algorithmic bytes per launch
     V = int(np.prod(DIMS))
-    bytes_per_site = NRHS * 8 * 12 * 16 + 4 * 9 * 8  # 8 spinor passes of 16-byte complex, float links once
+    bytes_per_site = NRHS * 8 * 12 * 16 + 4 * 9 * 16  # 8 spinor passes of 16-byte complex, float-pair links once
     alg_bytes = V * bytes_per_site
     n_st = st["stencil_launches"]
     st_ms = st["stencil_ms"] / max(n_st, 1)

@@ -64,9 +64,9 @@ extern "C" {
 #define OV_PREC_FP64 0  /* double vectors and links, double arithmetic */
 #define OV_PREC_FP32 1  /* float vectors and links, float stencil; dot products, norms and all
                            Krylov coefficients accumulated and kept in double */
-#define OV_PREC_DF64 2  /* float links (rounded once), vectors as unevaluated float pairs
-                           (hi + lo, ~48-bit significand) with error-free float arithmetic
-                           (Dekker 1971; Knuth TAOCP vol. 2 TwoSum); coefficients in double */
+#define OV_PREC_DF64 2  /* links and vectors as unevaluated float pairs (hi + lo, ~48-bit
+                           significand) with error-free float arithmetic (Dekker 1971;
+                           Knuth TAOCP vol. 2 TwoSum); coefficients in double */
 
 #define OV_MEM_HOST 0
 #define OV_MEM_DEVICE 1
@@ -105,7 +105,15 @@ typedef struct {
                            also uses plain launches) [8] */
   int timing;           /* 1: record CUDA events around every stencil / update / inner / recombination
                            launch on the handle's stream and accumulate their durations (ov_get_stats) [0] */
+  int inner_arith;      /* arithmetic of the inner level's serial parts (the tridiagonal solves with
+                           H_k, the Gauss-Jordan inversions of Roberts-Higham): OV_INNER_DF64 (float
+                           pairs on the float pipes, ~2^-48 per operation) or OV_INNER_FP64
+                           [OV_INNER_DF64]; the inner Krylov vectors, coefficients and results are
+                           double either way */
 } ov_opts;
+
+#define OV_INNER_DF64 0
+#define OV_INNER_FP64 1
 
 /* Launch counts and (with opts.timing) device time per kernel class, accumulated over
  * calls since the last ov_reset_stats. Times are CUDA-event durations on the handle's
@@ -141,7 +149,8 @@ const char* ov_strerror(int code);
 
 /* Create a handle for one gauge field: validates -2 < m_w < 0 (Sec. 1), copies the links
  * (canonical layout, `links_mem` says host or device) into handle-owned device memory in
- * the kernel layout (t-boundary sign folded in; rounded to float for FP32/DF64), and
+ * the kernel layout (t-boundary sign folded in; rounded to float for FP32, split into
+ * float pairs for DF64), and
  * records mu. stream: a cudaStream_t or NULL. opts may be NULL (defaults). */
 int ov_create(ov_handle** h, const ov_geom* geom, const void* links, int links_mem,
               double m_w, double mu, const ov_opts* opts, void* stream);

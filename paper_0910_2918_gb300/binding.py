@@ -26,6 +26,8 @@ OV_ERR_TOO_LARGE = -7
 OV_PREC_FP64 = 0
 OV_PREC_FP32 = 1
 OV_PREC_DF64 = 2
+OV_INNER_DF64 = 0
+OV_INNER_FP64 = 1
 PRECISIONS = {"fp64": OV_PREC_FP64, "fp32": OV_PREC_FP32, "df64": OV_PREC_DF64}
 
 OV_MEM_HOST = 0
@@ -45,7 +47,7 @@ class ov_opts(ctypes.Structure):
                 ("recombination", ctypes.c_int), ("rh_tol", ctypes.c_double), ("rh_maxit", ctypes.c_int),
                 ("breakdown_tol", ctypes.c_double), ("inner_dl", ctypes.c_int), ("k_fixed", ctypes.c_int),
                 ("check_schedule", ctypes.c_int), ("block_size", ctypes.c_int), ("graph_steps", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("inner_arith", ctypes.c_int)]
 
 
 class ov_stats(ctypes.Structure):

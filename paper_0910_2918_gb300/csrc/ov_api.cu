@@ -239,6 +239,7 @@ extern "C" void ov_default_opts(ov_opts* o) {
   o->block_size = 0;
   o->graph_steps = 8;
   o->timing = 0;
+  o->inner_arith = OV_INNER_DF64;
 }
 
 extern "C" const char* ov_strerror(int code) {
@@ -260,7 +261,7 @@ static int check_opts(const ov_opts& o) {
       o.first_check < 0 || o.recombination < 0 || o.recombination > 2 || !(o.breakdown_tol >= 0) ||
       o.check_schedule < 0 || o.check_schedule > 1 ||
       (o.block_size != 0 && o.block_size != 64 && o.block_size != 128 && o.block_size != 256) ||
-      o.graph_steps < 0 || o.graph_steps > 256)
+      o.graph_steps < 0 || o.graph_steps > 256 || o.inner_arith < 0 || o.inner_arith > 1)
     return OV_ERR_ARG;
   return OV_OK;
 }
@@ -286,6 +287,25 @@ __global__ void k_links(Geometry g, int anti, const double2* __restrict__ in, T*
       o.x = sg * z.x;
       o.y = sg * z.y;
       out[(size_t)(nu * 9 + e) * g.V + s] = o;
+    }
+  }
+}
+
+// double-float links: the float pairs (hi, lo) with hi + lo = U to 2^-48 relative,
+// stored as two planes [4][9][V] of float2 (hi first, then lo)
+__global__ void k_links_df(Geometry g, int anti, const double2* __restrict__ in, float2* out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int t = s / (g.Lx * g.Ly * g.Lz);
+  float2* lo = out + (size_t)36 * g.V;
+  for (int nu = 0; nu < 4; ++nu) {
+    const double sg = (nu == 3 && anti && t == g.Lt - 1) ? -1.0 : 1.0;
+    for (int e = 0; e < 9; ++e) {
+      const double2 z = in[((size_t)s * 4 + nu) * 9 + e];
+      const double x = sg * z.x, y = sg * z.y;
+      const float xh = (float)x, yh = (float)y;
+      out[(size_t)(nu * 9 + e) * g.V + s] = make_float2(xh, yh);
+      lo[(size_t)(nu * 9 + e) * g.V + s] = make_float2((float)(x - (double)xh), (float)(y - (double)yh));
     }
   }
 }
@@ -334,11 +354,14 @@ extern "C" int ov_create(ov_handle** hp, const ov_geom* geom, const void* links,
     if (cudaMemcpyAsync(tmp.p, links, canon, cudaMemcpyHostToDevice, h->st) != cudaSuccess) return fail(OV_ERR_CUDA);
     src = (const double2*)tmp.p;
   }
-  const size_t lb = (h->prec == OV_PREC_FP64 ? sizeof(double2) : sizeof(float2)) * 36 * (size_t)V;
+  // FP64: double links; FP32: float links; DF64: float hi and lo planes
+  const size_t lb = (h->prec == OV_PREC_FP32 ? 1 : 2) * sizeof(float2) * 36 * (size_t)V;
   if (grow(L.links, lb) != cudaSuccess) return fail(OV_ERR_NOMEM);
   const int nb = (int)((V + 127) / 128);
   if (h->prec == OV_PREC_FP64)
     k_links<double2><<<nb, 128, 0, h->st>>>(L.g, h->antiperiodic, src, (double2*)L.links.p);
+  else if (h->prec == OV_PREC_DF64)
+    k_links_df<<<nb, 128, 0, h->st>>>(L.g, h->antiperiodic, src, (float2*)L.links.p);
   else
     k_links<float2><<<nb, 128, 0, h->st>>>(L.g, h->antiperiodic, src, (float2*)L.links.p);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->st) != cudaSuccess) return fail(OV_ERR_CUDA);
@@ -439,6 +462,7 @@ static InnerWork inner_work(ov_handle* h) {
   w.perm = (int*)h->iperm.p;
   w.fail = (int*)h->ifail.p;
   w.ld = h->inner_ld;  // Q rows per problem, as allocated by ensure_inner
+  w.arith = h->o.inner_arith;
   return w;
 }
 

@@ -472,6 +472,527 @@ __global__ void __launch_bounds__(1024) k_rh(int count, int dense_m, const doubl
   for (int i = tid; i < m; i += nth) w.s[(size_t)mid * kMaxL + i] = Sg[(size_t)i * m];
 }
 
+// ------------------------------------------------- Roberts-Higham in double-float
+// The same iteration and Gauss-Jordan elimination as k_rh, with the matrix held as float
+// pairs (hi + lo, ~48-bit significand) and all arithmetic on the float pipes: on GB300 a
+// warp-wide FP64 instruction issues at ~1/64 of the float rate, and the elimination is
+// pure multiply-add. Products are formed exactly (p = a*b, e = fma(a, b, -p), cross terms
+// folded into e) and each output is renormalised once; the pivot reciprocal takes one
+// Newton step r = x + x (1 - d x) from the float reciprocal x, which doubles its 24
+// correct bits. Pivots are chosen on the high words.
+struct cdf {
+  df64 re, im;
+};
+
+// a + x1 y1 + x2 y2
+__device__ __forceinline__ df64 df_axpy2(df64 a, df64 x1, df64 y1, df64 x2, df64 y2) {
+  const float p1 = __fmul_rn(x1.hi, y1.hi);
+  float e1 = __fmaf_rn(x1.hi, y1.hi, -p1);
+  e1 = __fmaf_rn(x1.hi, y1.lo, e1);
+  e1 = __fmaf_rn(x1.lo, y1.hi, e1);
+  const float p2 = __fmul_rn(x2.hi, y2.hi);
+  float e2 = __fmaf_rn(x2.hi, y2.hi, -p2);
+  e2 = __fmaf_rn(x2.hi, y2.lo, e2);
+  e2 = __fmaf_rn(x2.lo, y2.hi, e2);
+  const df64 s = df_two_sum(a.hi, p1);
+  const df64 t = df_two_sum(s.hi, p2);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, s.lo), t.lo), __fadd_rn(e1, e2));
+  return df_fast_two_sum(t.hi, lo);
+}
+// a + x y
+__device__ __forceinline__ df64 df_axpy1(df64 a, df64 x, df64 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const df64 s = df_two_sum(a.hi, p);
+  return df_fast_two_sum(s.hi, __fadd_rn(__fadd_rn(a.lo, s.lo), e));
+}
+__device__ __forceinline__ df64 df_recip(df64 d) {
+  const float x = __frcp_rn(d.hi);
+  const df64 e = df64{1.f, 0.f} - d * x;
+  return df64{x, 0.f} + e * x;
+}
+
+__device__ __forceinline__ cdf e_load(const float4* p) {
+  const float4 v = *p;
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ df64 e_load(const float2* p) {
+  const float2 v = *p;
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void e_store(float4* p, cdf a) { *p = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+__device__ __forceinline__ void e_store(float2* p, df64 a) { *p = make_float2(a.hi, a.lo); }
+__device__ __forceinline__ float e_abs2hi(cdf a) { return a.re.hi * a.re.hi + a.im.hi * a.im.hi; }
+__device__ __forceinline__ float e_abs2hi(df64 a) { return a.hi * a.hi; }
+__device__ __forceinline__ cdf e_zero(cdf) { return {df_zero(), df_zero()}; }
+__device__ __forceinline__ df64 e_zero(df64) { return df_zero(); }
+// w - f r
+__device__ __forceinline__ cdf e_submul(cdf w, cdf f, cdf r) {
+  return {df_axpy2(w.re, -f.re, r.re, f.im, r.im), df_axpy2(w.im, -f.re, r.im, -f.im, r.re)};
+}
+__device__ __forceinline__ df64 e_submul(df64 w, df64 f, df64 r) { return df_axpy1(w, -f, r); }
+__device__ __forceinline__ cdf e_mul(cdf a, cdf b) {
+  return {df_axpy2(df_zero(), a.re, b.re, -a.im, b.im), df_axpy2(df_zero(), a.re, b.im, a.im, b.re)};
+}
+__device__ __forceinline__ df64 e_mul(df64 a, df64 b) { return a * b; }
+__device__ __forceinline__ cdf e_inv(cdf a) {
+  const df64 r = df_recip(df_axpy2(df_zero(), a.re, a.re, a.im, a.im));
+  return {a.re * r, -(a.im * r)};
+}
+__device__ __forceinline__ df64 e_inv(df64 a) { return df_recip(a); }
+// (a + b) / 2 and |(a + b) / 2 - a|^2, |(a + b) / 2|^2 (high words)
+__device__ __forceinline__ cdf e_avg(cdf a, cdf b, float& d2, float& n2) {
+  const cdf s = {df_half(a.re + b.re), df_half(a.im + b.im)};
+  const float dr = __fsub_rn(s.re.hi, a.re.hi), di = __fsub_rn(s.im.hi, a.im.hi);
+  d2 += dr * dr + di * di;
+  n2 += e_abs2hi(s);
+  return s;
+}
+__device__ __forceinline__ df64 e_avg(df64 a, df64 b, float& d2, float& n2) {
+  const df64 s = df_half(a + b);
+  const float d = __fsub_rn(s.hi, a.hi);
+  d2 += d * d;
+  n2 += s.hi * s.hi;
+  return s;
+}
+__device__ __forceinline__ bool e_finite(cdf a) {
+  return isfinite(a.re.hi) && isfinite(a.re.lo) && isfinite(a.im.hi) && isfinite(a.im.lo);
+}
+__device__ __forceinline__ bool e_finite(df64 a) { return isfinite(a.hi) && isfinite(a.lo); }
+__device__ __forceinline__ double2 e_to2(cdf a) { return make_double2(df_to_double(a.re), df_to_double(a.im)); }
+__device__ __forceinline__ double2 e_to2(df64 a) { return make_double2(df_to_double(a), 0.0); }
+__device__ __forceinline__ cdf e_from2(double2 v, cdf) { return {df_from_double(v.x), df_from_double(v.y)}; }
+__device__ __forceinline__ df64 e_from2(double2 v, df64) { return df_from_double(v.x); }
+
+template <bool CPLX>
+struct RhDf;
+template <> struct RhDf<true> { using E = cdf; using St = float4; };
+template <> struct RhDf<false> { using E = df64; using St = float2; };
+
+template <bool CPLX>
+__global__ void __launch_bounds__(1024) k_rh_df(int count, int dense_m, const double2* __restrict__ dense_T,
+                                                InnerWork w, int dl, double rh_tol, int rh_maxit, int mid0) {
+  using E = typename RhDf<CPLX>::E;
+  using St = typename RhDf<CPLX>::St;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int mid = mid0 + blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  int m;
+  if (dense_m > 0) {
+    m = dense_m;
+  } else {
+    const int prob = mid % count;
+    const int le = w.leff[prob];
+    m = mid < count ? le : le - dl;
+  }
+  if (m <= 0) {
+    if (tid == 0) { w.rh_ok[mid] = m == 0 ? 0 : 1; w.rh_its[mid] = 0; }
+    return;
+  }
+  St* W = (St*)smem;                  // m x m working matrix
+  St* col = W + (size_t)m * m;        // column buffer / reduction scratch
+  double* red = (double*)col;
+  int* piv_slot = (int*)col;
+  // global S_n (row-major, leading dim m) in the float-pair storage, in the problem's
+  // double2 slot (16 bytes per element)
+  St* Sg = (St*)(w.S + (size_t)mid * kMaxL * kMaxL);
+  int* perm = w.perm + (size_t)mid * kMaxL;
+  const E ez = e_zero(E{});
+  for (int e = tid; e < m * m; e += nth) {
+    const int i = e / m, j = e % m;
+    double2 v = make_double2(0.0, 0.0);
+    if (dense_m > 0) {
+      v = dense_T[(size_t)mid * m * m + e];
+    } else {
+      const double2* T = w.T + (size_t)(mid % count) * kMaxL * 3;
+      if (i == j) v = T[i * 3 + 0];
+      else if (i == j + 1) v = T[i * 3 + 1];
+      else if (j == i + 1) v = T[j * 3 + 2];
+    }
+    e_store(&Sg[e], e_from2(v, ez));
+  }
+  __syncthreads();
+  int ok = 0, it = 0;
+  for (it = 1; it <= rh_maxit; ++it) {
+    for (int e = tid; e < m * m; e += nth) W[e] = Sg[e];
+    __syncthreads();
+    bool singular = false;
+    for (int j = 0; j < m; ++j) {
+      if (tid < 32) {
+        float best = -1.f;
+        int bi = j;
+        for (int i = j + tid; i < m; i += 32) {
+          const float a2 = e_abs2hi(e_load(&W[(size_t)i * m + j]));
+          if (a2 > best) { best = a2; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (tid == 0) piv_slot[0] = best > 0.f ? bi : -1;
+      }
+      __syncthreads();
+      const int p = piv_slot[0];
+      __syncthreads();
+      if (p < 0) { singular = true; break; }
+      if (p != j)
+        for (int c = tid; c < m; c += nth) {
+          const St t = W[(size_t)j * m + c];
+          W[(size_t)j * m + c] = W[(size_t)p * m + c];
+          W[(size_t)p * m + c] = t;
+        }
+      if (tid == 0) perm[j] = p;
+      __syncthreads();
+      const E inv = e_inv(e_load(&W[(size_t)j * m + j]));
+      __syncthreads();
+      for (int c = tid; c < m; c += nth)
+        e_store(&W[(size_t)j * m + c], c == j ? inv : e_mul(e_load(&W[(size_t)j * m + c]), inv));
+      for (int i = tid; i < m; i += nth) col[i] = i == j ? St{} : W[(size_t)i * m + j];
+      __syncthreads();
+      for (int i = tid; i < m; i += nth)
+        if (i != j) W[(size_t)i * m + j] = St{};
+      __syncthreads();
+      {
+        const int tx = tid & 31, ty = tid >> 5;
+        E rowj[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int c = tx + 32 * b;
+          rowj[b] = c < m ? e_load(&W[(size_t)j * m + c]) : ez;
+        }
+        for (int i = ty; i < m; i += 32) {
+          if (i == j) continue;
+          const E f = e_load(&col[i]);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int c = tx + 32 * b;
+            if (c < m) e_store(&W[(size_t)i * m + c], e_submul(e_load(&W[(size_t)i * m + c]), f, rowj[b]));
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (singular) { ok = 0; break; }
+    for (int j = m - 1; j >= 0; --j) {
+      const int p = perm[j];
+      if (p != j)
+        for (int i = tid; i < m; i += nth) {
+          const St t = W[(size_t)i * m + j];
+          W[(size_t)i * m + j] = W[(size_t)i * m + p];
+          W[(size_t)i * m + p] = t;
+        }
+      __syncthreads();
+    }
+    float d2 = 0.f, n2 = 0.f;
+    bool fin = true;
+    for (int e = tid; e < m * m; e += nth) {
+      const E s1 = e_avg(e_load(&Sg[e]), e_load(&W[e]), d2, n2);
+      fin = fin && e_finite(s1);
+      e_store(&Sg[e], s1);
+    }
+    __syncthreads();
+    double dif = warp_sum((double)d2);
+    double nrm = warp_sum((double)n2);
+    const int fin_all = __syncthreads_and(fin ? 1 : 0);
+    if ((tid & 31) == 0) { red[(tid >> 5) * 2] = dif; red[(tid >> 5) * 2 + 1] = nrm; }
+    __syncthreads();
+    double D = 0.0, N = 0.0;
+    for (int q = 0; q < (nth >> 5); ++q) { D += red[2 * q]; N += red[2 * q + 1]; }
+    __syncthreads();
+    if (!fin_all || !isfinite(D) || !isfinite(N)) { ok = 0; break; }
+    if (sqrt(D) <= rh_tol * sqrt(N)) { ok = 1; break; }
+  }
+  if (tid == 0) {
+    w.rh_ok[mid] = ok;
+    w.rh_its[mid] = it > rh_maxit ? rh_maxit : it;
+  }
+  for (int i = tid; i < m; i += nth) w.s[(size_t)mid * kMaxL + i] = e_to2(e_load(&Sg[(size_t)i * m]));
+  if (CPLX && dense_m > 0) {
+    // the caller reads S as double2: convert in place (same 16-byte slot per element)
+    __syncthreads();
+    double2* Sd = w.S + (size_t)mid * kMaxL * kMaxL;
+    for (int e = tid; e < m * m; e += nth) {
+      const E v = e_load(&Sg[e]);
+      Sd[e] = e_to2(v);
+    }
+  }
+}
+
+// ------------------------------------------------- inner Krylov in double-float
+// k_inner with every operation on the float pipes: the tridiagonal factorisation and the
+// two serial solves per step (the critical path of the inner level) and the vector
+// updates in float pairs, the block reductions in float pairs. Square roots take one
+// Newton step y + (x - y^2) / (2 y) from the float root, quotients multiply by the
+// refined reciprocal (Karp and Markstein, ACM TOMS 23 (1997)). Outputs (T, Q) are double.
+__device__ __forceinline__ cdf c_add(cdf a, cdf b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cdf c_conj(cdf a) { return {a.re, -a.im}; }
+__device__ __forceinline__ cdf c_scale(cdf a, df64 s) { return {a.re * s, a.im * s}; }
+// a + f r
+__device__ __forceinline__ cdf c_addmul(cdf a, cdf f, cdf r) {
+  return {df_axpy2(a.re, f.re, r.re, -f.im, r.im), df_axpy2(a.im, f.re, r.im, f.im, r.re)};
+}
+// a + conj(f) r
+__device__ __forceinline__ cdf c_addmulc(cdf a, cdf f, cdf r) {
+  return {df_axpy2(a.re, f.re, r.re, f.im, r.im), df_axpy2(a.im, f.re, r.im, -f.im, r.re)};
+}
+// a - conj(f) r
+__device__ __forceinline__ cdf c_submulc(cdf a, cdf f, cdf r) {
+  return {df_axpy2(a.re, -f.re, r.re, -f.im, r.im), df_axpy2(a.im, -f.re, r.im, f.im, r.re)};
+}
+__device__ __forceinline__ df64 df_sqrt(df64 x) {
+  if (!(x.hi > 0.f)) return df_zero();
+  const float y = __fsqrt_rn(x.hi);
+  const df64 e = x - df_prod(y, y);
+  return df_two_sum(y, __fmul_rn(e.hi, __fdiv_rn(0.5f, y)));
+}
+__device__ __forceinline__ df64 block_sum_df(df64 v, df64* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  df64 s = df_zero();
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = s + red[w];
+  return s;
+}
+
+struct InnerSmemDf {
+  float4 *d, *a, *c, *uinv, *u1, *u2, *l, *q, *qp, *w, *wp, *u, *z;
+  unsigned char* sw;
+  df64* red;
+};
+
+__device__ bool tri_factor_df(const InnerSmemDf& S, int k) {
+  const cdf zero = {df_zero(), df_zero()};
+  cdf dd = e_load(&S.d[0]);
+  cdf ee = k > 1 ? e_load(&S.c[0]) : zero;
+  for (int m = 0; m < k - 1; ++m) {
+    const cdf an = e_load(&S.a[m + 1]), dn = e_load(&S.d[m + 1]);
+    const cdf cn = (m + 1 <= k - 2) ? e_load(&S.c[m + 1]) : zero;
+    cdf r0, r1, r2, lm;
+    if (e_abs2hi(dd) >= e_abs2hi(an)) {
+      if (e_abs2hi(dd) == 0.f) return false;
+      lm = e_mul(an, e_inv(dd));
+      r0 = dd; r1 = ee; r2 = zero;
+      dd = e_submul(dn, lm, ee);
+      ee = cn;
+      S.sw[m] = 0;
+    } else {
+      lm = e_mul(dd, e_inv(an));
+      r0 = an; r1 = dn; r2 = cn;
+      dd = e_submul(ee, lm, dn);
+      ee = e_submul(zero, lm, cn);
+      S.sw[m] = 1;
+    }
+    e_store(&S.uinv[m], e_inv(r0));
+    e_store(&S.u1[m], r1);
+    e_store(&S.u2[m], r2);
+    e_store(&S.l[m], lm);
+  }
+  if (e_abs2hi(dd) == 0.f) return false;
+  e_store(&S.uinv[k - 1], e_inv(dd));
+  return true;
+}
+
+// x = H^{-1} b (row interchanges between neighbours, then the banded U)
+__device__ void tri_solve_df(const InnerSmemDf& S, int k, const float4* b, float4* x) {
+  cdf cur = e_load(&b[0]);
+#pragma unroll 2
+  for (int m = 0; m < k - 1; ++m) {
+    const cdf nb = e_load(&b[m + 1]);
+    const bool sw = S.sw[m];
+    const cdf bsel = sw ? nb : cur, asel = sw ? cur : nb;
+    e_store(&x[m], bsel);
+    cur = e_submul(asel, e_load(&S.l[m]), bsel);
+  }
+  cdf x1 = e_mul(cur, e_load(&S.uinv[k - 1]));
+  e_store(&x[k - 1], x1);
+  if (k < 2) return;
+  cdf x0 = e_mul(e_submul(e_load(&x[k - 2]), e_load(&S.u1[k - 2]), x1), e_load(&S.uinv[k - 2]));
+  e_store(&x[k - 2], x0);
+#pragma unroll 2
+  for (int m = k - 3; m >= 0; --m) {
+    const cdf f = e_submul(e_load(&x[m]), e_load(&S.u2[m]), x1);
+    const cdf xm = e_mul(e_submul(f, e_load(&S.u1[m]), x0), e_load(&S.uinv[m]));
+    e_store(&x[m], xm);
+    x1 = x0;
+    x0 = xm;
+  }
+}
+
+// z = H^{-dag} b: U^dag g = b forwards, then the interchanges' adjoints backwards
+__device__ void tri_solve_dag_df(const InnerSmemDf& S, int k, const float4* b, float4* z) {
+  const cdf zero = {df_zero(), df_zero()};
+  cdf z1 = zero, z2 = zero;  // z[m-1], z[m-2]
+#pragma unroll 2
+  for (int m = 0; m < k; ++m) {
+    cdf t = e_load(&b[m]);
+    if (m >= 1) t = c_submulc(t, e_load(&S.u1[m - 1]), z1);
+    if (m >= 2) t = c_submulc(t, e_load(&S.u2[m - 2]), z2);
+    const cdf zm = e_mul(t, c_conj(e_load(&S.uinv[m])));
+    e_store(&z[m], zm);
+    z2 = z1;
+    z1 = zm;
+  }
+  cdf gn = z1;  // current z[m + 1]
+#pragma unroll 2
+  for (int m = k - 2; m >= 0; --m) {
+    const cdf v = c_submulc(e_load(&z[m]), e_load(&S.l[m]), gn);
+    const bool sw = S.sw[m];
+    e_store(&z[m + 1], sw ? v : gn);
+    gn = sw ? gn : v;
+  }
+  e_store(&z[0], gn);
+}
+
+__global__ void __launch_bounds__(kInnerThreads) k_inner_df(const int* __restrict__ k_dev,
+                                                            const int* __restrict__ l_dev, int hermitian,
+                                                            const double2* __restrict__ alp,
+                                                            const double2* __restrict__ bet,
+                                                            const double2* __restrict__ gam, int ldc, InnerWork w) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int prob = blockIdx.x;
+  const int k = k_dev[prob];
+  const int l = min(l_dev[prob], k);
+  const int tid = threadIdx.x;
+  InnerSmemDf S;
+  {
+    float4* base = (float4*)smem;
+    S.d = base; S.a = base + k; S.c = base + 2 * k;
+    S.uinv = base + 3 * k; S.u1 = base + 4 * k; S.u2 = base + 5 * k; S.l = base + 6 * k;
+    S.q = base + 7 * k; S.qp = base + 8 * k; S.w = base + 9 * k; S.wp = base + 10 * k;
+    S.u = base + 11 * k; S.z = base + 12 * k;
+    S.red = (df64*)(base + 13 * k);
+    S.sw = (unsigned char*)(S.red + 32);
+  }
+  const cdf zero = {df_zero(), df_zero()};
+  const double2* al = alp + (size_t)prob * ldc;
+  const double2* be = bet + (size_t)prob * ldc;
+  const double2* ga = gam + (size_t)prob * ldc;
+  for (int m = tid; m < k; m += blockDim.x) {
+    double2 dm = al[m + 1];
+    double2 am = m >= 1 ? be[m + 1] : make_double2(0.0, 0.0);
+    double2 cm = m + 1 < k ? ga[m + 2] : make_double2(0.0, 0.0);
+    if (hermitian) { dm.y = 0.0; am.y = 0.0; cm = m + 1 < k ? make_double2(be[m + 2].x, 0.0) : cm; }
+    e_store(&S.d[m], e_from2(dm, zero));
+    e_store(&S.a[m], e_from2(am, zero));
+    e_store(&S.c[m], e_from2(cm, zero));
+    const cdf q0 = m == 0 ? cdf{{1.f, 0.f}, df_zero()} : zero;
+    e_store(&S.q[m], q0);
+    e_store(&S.w[m], q0);
+    e_store(&S.qp[m], zero);
+    e_store(&S.wp[m], zero);
+  }
+  __syncthreads();
+  __shared__ int s_ok;
+  if (tid == 0) s_ok = tri_factor_df(S, k) ? 1 : 0;
+  __syncthreads();
+  if (!s_ok) {
+    if (tid == 0) { w.fail[prob] = 1; w.leff[prob] = 0; }
+    return;
+  }
+  double2* Q = w.Q + (size_t)prob * w.ld * kMaxL;
+  double2* T = w.T + (size_t)prob * kMaxL * 3;
+  df64 b_i = df_zero();
+  cdf g_i = zero;
+  int done = 0;
+  const float exhaust_tol = 1e-13f;
+  for (int i = 0; i < l; ++i) {
+    for (int m = tid; m < k; m += blockDim.x) Q[(size_t)m * kMaxL + i] = e_to2(e_load(&S.q[m]));
+    if (tid == 0) tri_solve_df(S, k, S.q, S.u);
+    if (!hermitian && tid == 32) tri_solve_dag_df(S, k, S.w, S.z);
+    __syncthreads();
+    float mq2 = 0.f;
+    for (int m = tid; m < k; m += blockDim.x) {
+      cdf t = e_mul(e_load(&S.d[m]), e_load(&S.q[m]));
+      if (m >= 1) t = c_addmul(t, e_load(&S.a[m]), e_load(&S.q[m - 1]));
+      if (m + 1 < k) t = c_addmul(t, e_load(&S.c[m]), e_load(&S.q[m + 1]));
+      t = c_add(t, e_load(&S.u[m]));
+      mq2 += e_abs2hi(t);
+      const cdf qp = e_load(&S.qp[m]);
+      e_store(&S.u[m], hermitian ? e_submul(t, cdf{b_i, df_zero()}, qp) : e_submul(t, g_i, qp));  // p
+      if (!hermitian) {
+        cdf y = e_mul(c_conj(e_load(&S.d[m])), e_load(&S.w[m]));
+        if (m >= 1) y = c_addmulc(y, e_load(&S.c[m - 1]), e_load(&S.w[m - 1]));
+        if (m + 1 < k) y = c_addmulc(y, e_load(&S.a[m + 1]), e_load(&S.w[m + 1]));
+        y = c_add(y, e_load(&S.z[m]));
+        e_store(&S.z[m], e_submul(y, cdf{b_i, df_zero()}, e_load(&S.wp[m])));  // r
+      }
+    }
+    __syncthreads();
+    // alpha = w^dag p (q^dag p in the Hermitian case)
+    df64 are = df_zero(), aim = df_zero();
+    for (int m = tid; m < k; m += blockDim.x) {
+      const cdf wm = e_load(hermitian ? &S.q[m] : &S.w[m]);
+      const cdf pm = e_load(&S.u[m]);
+      are = df_axpy2(are, wm.re, pm.re, wm.im, pm.im);
+      aim = df_axpy2(aim, wm.re, pm.im, -wm.im, pm.re);
+    }
+    are = block_sum_df(are, S.red);
+    aim = hermitian ? df_zero() : block_sum_df(aim, S.red);
+    const df64 mqn = df_sqrt(block_sum_df(df64{mq2, 0.f}, S.red));
+    const cdf a_i = {are, aim};
+    if (tid == 0) T[i * 3 + 0] = e_to2(a_i);
+    done = i + 1;
+    if (i == l - 1) break;
+    // q~ = p - alpha q ; w~ = r - conj(alpha) w ; delta = w~^dag q~
+    df64 dre = df_zero(), dim = df_zero(), n2 = df_zero();
+    for (int m = tid; m < k; m += blockDim.x) {
+      const cdf qt = e_submul(e_load(&S.u[m]), a_i, e_load(&S.q[m]));
+      e_store(&S.u[m], qt);
+      if (hermitian) {
+        n2 = df_axpy2(n2, qt.re, qt.re, qt.im, qt.im);
+      } else {
+        const cdf wt = c_submulc(e_load(&S.z[m]), a_i, e_load(&S.w[m]));
+        e_store(&S.z[m], wt);
+        dre = df_axpy2(dre, wt.re, qt.re, wt.im, qt.im);
+        dim = df_axpy2(dim, wt.re, qt.im, -wt.im, qt.re);
+      }
+    }
+    df64 bn;
+    cdf gn;
+    if (hermitian) {
+      bn = df_sqrt(block_sum_df(n2, S.red));
+      gn = {bn, df_zero()};
+    } else {
+      dre = block_sum_df(dre, S.red);
+      dim = block_sum_df(dim, S.red);
+      bn = df_sqrt(df_sqrt(df_axpy2(df_zero(), dre, dre, dim, dim)));
+      const df64 rb = bn.hi > 0.f ? df_recip(bn) : df_zero();
+      gn = {dre * rb, dim * rb};
+    }
+    if (!(bn.hi > exhaust_tol * mqn.hi)) break;  // inner space exhausted: T_i is exact
+    if (tid == 0) {
+      T[(i + 1) * 3 + 1] = make_double2(df_to_double(bn), 0.0);
+      T[(i + 1) * 3 + 2] = e_to2(gn);
+    }
+    const cdf wdiv = e_inv(c_conj(gn));
+    const df64 rbn = df_recip(bn);
+    __syncthreads();
+    for (int m = tid; m < k; m += blockDim.x) {
+      e_store(&S.qp[m], e_load(&S.q[m]));
+      e_store(&S.q[m], c_scale(e_load(&S.u[m]), rbn));
+      if (!hermitian) {
+        e_store(&S.wp[m], e_load(&S.w[m]));
+        e_store(&S.w[m], e_mul(e_load(&S.z[m]), wdiv));
+      }
+    }
+    b_i = bn;
+    g_i = gn;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    w.leff[prob] = done;
+    T[0 * 3 + 1] = make_double2(0.0, 0.0);
+    T[0 * 3 + 2] = make_double2(0.0, 0.0);
+    w.fail[prob] = 0;
+  }
+}
+
 // ------------------------------------------------------------ combine
 __global__ void __launch_bounds__(kInnerThreads) k_combine(int count, const int* __restrict__ k_dev,
                                                            const int* __restrict__ l_dev, InnerWork w, int dl,
@@ -555,10 +1076,16 @@ cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermiti
                       int* rh_iters, int phase, cudaStream_t st) {
   cudaError_t e;
   if (phase != 2) {
-    const size_t sm = inner_smem(w.ld);
-    e = cudaFuncSetAttribute(k_inner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_inner<<<count, kInnerThreads, sm, st>>>(k_dev, l_dev, hermitian, alp, bet, gam, ldc, w);
+    const size_t sm = inner_smem(w.ld);  // float pairs take the bytes of the doubles they replace
+    if (w.arith == OV_INNER_DF64) {
+      e = cudaFuncSetAttribute(k_inner_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      k_inner_df<<<count, kInnerThreads, sm, st>>>(k_dev, l_dev, hermitian, alp, bet, gam, ldc, w);
+    } else {
+      e = cudaFuncSetAttribute(k_inner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      k_inner<<<count, kInnerThreads, sm, st>>>(k_dev, l_dev, hermitian, alp, bet, gam, ldc, w);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // phase 0: both Roberts-Higham sets (the matrices and their leading l - dl blocks);
@@ -569,7 +1096,18 @@ cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermiti
   const size_t esz = hermitian ? sizeof(double) : sizeof(double2);
   // matrix + column buffer (which also holds the 64-double reduction scratch)
   const size_t rsm = (size_t)kMaxL * kMaxL * esz + std::max<size_t>(kMaxL * esz, 512);
-  if (hermitian) {
+  if (w.arith == OV_INNER_DF64) {
+    // float pairs take the bytes of the double elements they replace
+    if (hermitian) {
+      e = cudaFuncSetAttribute(k_rh_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+      if (e != cudaSuccess) return e;
+      k_rh_df<false><<<nmat, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit, mid0);
+    } else {
+      e = cudaFuncSetAttribute(k_rh_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+      if (e != cudaSuccess) return e;
+      k_rh_df<true><<<nmat, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit, mid0);
+    }
+  } else if (hermitian) {
     e = cudaFuncSetAttribute(k_rh<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
     if (e != cudaSuccess) return e;
     k_rh<false><<<nmat, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit, mid0);
@@ -587,9 +1125,16 @@ cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermiti
 cudaError_t run_rh_dense(int count, int m, const double2* T, double2* S, int* iters, int* ok, double rh_tol,
                          int rh_maxit, InnerWork& w, cudaStream_t st) {
   const size_t rsm = (size_t)m * m * sizeof(double2) + std::max<size_t>(m * sizeof(double2), 512);
-  cudaError_t e = cudaFuncSetAttribute(k_rh<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
-  if (e != cudaSuccess) return e;
-  k_rh<true><<<count, 1024, rsm, st>>>(count, m, T, w, 0, rh_tol, rh_maxit, 0);
+  cudaError_t e;
+  if (w.arith == OV_INNER_DF64) {
+    e = cudaFuncSetAttribute(k_rh_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    if (e != cudaSuccess) return e;
+    k_rh_df<true><<<count, 1024, rsm, st>>>(count, m, T, w, 0, rh_tol, rh_maxit, 0);
+  } else {
+    e = cudaFuncSetAttribute(k_rh<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    if (e != cudaSuccess) return e;
+    k_rh<true><<<count, 1024, rsm, st>>>(count, m, T, w, 0, rh_tol, rh_maxit, 0);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int i = 0; i < count; ++i) {
     e = cudaMemcpy2DAsync(S + (size_t)i * m * m, sizeof(double2) * m * m, w.S + (size_t)i * kMaxL * kMaxL,

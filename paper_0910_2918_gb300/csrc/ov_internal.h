@@ -133,6 +133,7 @@ struct InnerWork {
   int* perm;        // [2*count][kMaxL]
   int* fail;        // [count] singular H_k
   int ld;
+  int arith;        // OV_INNER_DF64 / OV_INNER_FP64: arithmetic of the serial solves and inversions
 };
 // Inner level for `count` problems whose tridiagonal coefficients live in device
 // arrays alp/bet/gam with leading dimension ldc (index j = 1..k as in Coefs, so the

@@ -307,13 +307,16 @@ __device__ __forceinline__ void hopping(cx<typename P::R> (&acc)[12], const type
 }
 
 // ---- double-float hopping in compensated form -------------------------------------------
-// The products U_ab h_b with float U and double-float h are summed as in the compensated
-// dot product of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26 (2005), "Dot2"): the
-// product of U with h.hi is exact as (p, e) (p = U*h.hi, e = fma(U, h.hi, -p)), U*h.lo is
-// folded into e with one FMA, the running sum takes p through TwoSum, and all error terms
-// are accumulated in the low word without renormalising. Sums are renormalised once, when
-// the hopping term is complete. Error: a few units of 2^-48 relative to the summed
-// magnitudes, as for the normalised pair arithmetic.
+// The links are double-float too: a plane of float hi parts and, 36 V elements further on,
+// a plane of lo parts (|lo| <= 2^-24 |hi|). The products U_ab h_b are summed as in the
+// compensated dot product of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26 (2005), "Dot2"):
+// the product of U.hi with h.hi is exact as (p, e) (p = U.hi*h.hi, e = fma(U.hi, h.hi, -p)),
+// U.hi*h.lo is folded into e with one FMA, the running sum takes p through TwoSum, and all
+// error terms are accumulated in the low word without renormalising; U.lo*h.hi, a term of
+// relative size 2^-24, is added to the low word in plain float arithmetic once per row
+// (the lo links are loaded with the hi links at the start of the hop).
+// Sums are renormalised once, when the hopping term is complete. Error: a few units of
+// 2^-48 relative to the summed magnitudes, as for the normalised pair arithmetic.
 struct dfu {  // unnormalised pair: value hi + lo
   float hi, lo;
 };
@@ -352,6 +355,7 @@ __device__ __forceinline__ void hopping_df(cx<df64> (&accn)[12], const float4* _
                                            const float2* __restrict__ links, const Geometry& g, int s,
                                            const int (&xc)[4], df64 ef, df64 eb) {
   const int V = g.V;
+  const float2* __restrict__ links_lo = links + (size_t)36 * V;
   cxu acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = {{0.f, 0.f}, {0.f, 0.f}};
@@ -364,11 +368,12 @@ __device__ __forceinline__ void hopping_df(cx<df64> (&accn)[12], const float4* _
     const int c = xc[0] * (nu == 0) + xc[1] * (nu == 1) + xc[2] * (nu == 2) + xc[3] * (nu == 3);
     const int sn = fwd ? (c == Ln - 1 ? s - (Ln - 1) * st : s + st) : (c == 0 ? s + (Ln - 1) * st : s - st);
     const int ls = fwd ? s : sn;
-    cx<float> u[9];
+    cx<float> u[9], ulo[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
       const int idx = fwd ? e : (e % 3) * 3 + e / 3;
       u[e] = lconj(ld_link(links + (size_t)(nu * 9 + idx) * V + ls), !fwd);
+      ulo[e] = lconj(ld_link(links_lo + (size_t)(nu * 9 + idx) * V + ls), !fwd);
     }
     const int b0s = c_bsrc[nu][0], b1s = c_bsrc[nu][1];
     const int b0q = (c_bph[nu][0] + (fwd ? 2 : 0)) & 3, b1q = (c_bph[nu][1] + (fwd ? 2 : 0)) & 3;
@@ -405,6 +410,20 @@ __device__ __forceinline__ void hopping_df(cx<df64> (&accn)[12], const float4* _
         madd_u(g1.im, ub.re, h1[b].im);
         madd_u(g1.im, ub.im, h1[b].re);
       }
+      // U.lo row a times h.hi, into the low words
+      float c0r = 0.f, c0i = 0.f, c1r = 0.f, c1i = 0.f;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const cx<float> ul = ulo[a * 3 + b];
+        c0r = __fmaf_rn(ul.re, h0[b].re.hi, __fmaf_rn(-ul.im, h0[b].im.hi, c0r));
+        c0i = __fmaf_rn(ul.re, h0[b].im.hi, __fmaf_rn(ul.im, h0[b].re.hi, c0i));
+        c1r = __fmaf_rn(ul.re, h1[b].re.hi, __fmaf_rn(-ul.im, h1[b].im.hi, c1r));
+        c1i = __fmaf_rn(ul.re, h1[b].im.hi, __fmaf_rn(ul.im, h1[b].re.hi, c1i));
+      }
+      g0.re.lo = __fadd_rn(g0.re.lo, c0r);
+      g0.im.lo = __fadd_rn(g0.im.lo, c0i);
+      g1.re.lo = __fadd_rn(g1.re.lo, c1r);
+      g1.im.lo = __fadd_rn(g1.im.lo, c1i);
       if (sc) {
         const cx<df64> n0 = cscale(cx<df64>{norm_u(g0.re), norm_u(g0.im)}, fac);
         const cx<df64> n1 = cscale(cx<df64>{norm_u(g1.re), norm_u(g1.im)}, fac);
@@ -448,8 +467,16 @@ __device__ __forceinline__ StepPtrs step_ptrs(const StepArgs& a) {
   return {j, vprev, vcur, wr + pb * (j & 1), wr + pb * ((j - 1) & 1)};
 }
 
+// The double-float step is capped at 128 registers a thread (16 warps an SM at every block
+// size): the hop body fits without spilling and the extra warps hide the load latency at
+// the start of each hop. The other precisions keep the compiler's choice.
+template <class P, int BS>
+constexpr int step_min_blocks() {
+  return P::id == PrecDF64::id ? 512 / BS : 1;
+}
+
 template <class P, int MODE, int BS>
-__global__ void __launch_bounds__(BS) k_step(StepArgs a) {
+__global__ void __launch_bounds__(BS, step_min_blocks<P, BS>()) k_step(StepArgs a) {
   using R = typename P::R;
   using V_t = typename P::vec_t;
   using L_t = typename P::link_t;

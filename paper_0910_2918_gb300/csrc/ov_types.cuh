@@ -3,7 +3,7 @@
 // Three arithmetic modes share one kernel source:
 //   PrecF64  - double vectors, double links, double arithmetic;
 //   PrecF32  - float vectors, float links, float stencil; reductions in double-float;
-//   PrecDF64 - vectors as unevaluated float pairs (hi + lo), float links, error-free
+//   PrecDF64 - vectors and links as unevaluated float pairs (hi + lo), error-free
 //              float arithmetic. The pair arithmetic is built from the exact
 //              transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2), Fast2Sum (Dekker
 //              1971) and the FMA product error p = a*b, e = fma(a, b, -p) (exact in

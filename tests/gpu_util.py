@@ -19,5 +19,6 @@ def oracle_sign(U, dims, m_w, mu, x, **kw):
 
 
 def links_for(prec, U):
-    """The operator a run of precision `prec` sees: float links are rounded once."""
-    return U if prec == "fp64" else oi.round_links_fp32(U)
+    """The operator a run of precision `prec` sees: FP32 rounds the links to float once;
+    double-float keeps them as float pairs (2^-48 relative), i.e. the FP64 operator."""
+    return oi.round_links_fp32(U) if prec == "fp32" else U

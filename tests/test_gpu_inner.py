@@ -17,10 +17,12 @@ def ov():
     return ov
 
 
-@pytest.fixture(scope="module")
-def handle(ov):
+@pytest.fixture(scope="module", params=["df64", "fp64"])
+def handle(ov, request):
+    """Both arithmetics of the inner level's serial parts (float pairs, the default, and FP64)."""
     dims = (2, 2, 2, 2)
-    h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0)
+    arith = ov.binding.OV_INNER_DF64 if request.param == "df64" else ov.binding.OV_INNER_FP64
+    h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0, opts=ov.make_opts(inner_arith=arith))
     yield h
     ov.ov_destroy(h)
 
@@ -116,3 +118,22 @@ def test_roberts_higham_singular_reports(ov, handle):
     T[0, :3, :3] = np.eye(3)
     rc, S, its = ov.ov_rh_sign(handle, T)
     assert rc == ov.binding.OV_ERR_RH_NOCONV
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_inner_arithmetics_agree(ov, mu):
+    """The float-pair and FP64 inner levels give the same converged c (1e-12) and the
+    same inner estimate in size."""
+    outers = [ritz(mu, k, seed=s) for k, s in ((200, 8), (120, 9))]
+    ks, A, B, G = pack(outers, 200)
+    dims = (2, 2, 2, 2)
+    out = {}
+    for arith in (ov.binding.OV_INNER_DF64, ov.binding.OV_INNER_FP64):
+        h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0, opts=ov.make_opts(inner_arith=arith))
+        out[arith] = ov.ov_inner_sign(h, ks, A, B, G, mu == 0.0, 110)
+        ov.ov_destroy(h)
+    (rd, cd, ed, _), (rf, cf, ef, _) = out[ov.binding.OV_INNER_DF64], out[ov.binding.OV_INNER_FP64]
+    assert rd == 0 and rf == 0
+    for i, k in enumerate(ks):
+        assert np.linalg.norm(cd[i, :k] - cf[i, :k]) / np.linalg.norm(cf[i, :k]) < 1e-12
+        assert ed[i] < 1e-10 and ef[i] < 1e-10

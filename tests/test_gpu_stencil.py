@@ -52,11 +52,10 @@ def test_stencil_full_size_bench_lattice(ov):
     """16^4, 12 point sources, the bench's launch shape (double-float)."""
     dims = (16, 16, 16, 16)
     U = oi.gauge_field(dims, "near_unit", 0, eps=0.3)
-    Ul = oi.round_links_fp32(U)
     x = oi.point_sources_12(dims)
     x[:, :] += 1e-3 * oi.gaussian_source(dims, 9)[None, :]
     y = np.zeros_like(x)
     with ov.Overlap(dims, U, -1.6, 0.2, "df64") as op:
         op.wilson_apply(x, y)
     for r in (0, 5, 11):
-        assert rel(y[r], dirac.A_apply(Ul, x[r], dims, -1.6, 0.2)) < 5e-14
+        assert rel(y[r], dirac.A_apply(U, x[r], dims, -1.6, 0.2)) < 5e-14
