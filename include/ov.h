@@ -209,7 +209,8 @@ int ov_inner_sign(ov_handle* h, int count, int ld, const int* k, const void* alp
                   double* est_inner, int* rh_iters);
 
 /* Roberts-Higham alone (Sec. 2, Eq. (Roberts)): S = sgn(T) for `count` dense m x m
- * matrices (row-major complex doubles, HOST memory, m <= 120), written to S (host).
+ * matrices (row-major complex doubles, HOST memory, m <= 120), written to S (host), with
+ * the Gauss-Jordan inversions in the handle's opts.inner_arith.
  * Returns OV_ERR_RH_NOCONV if any matrix did not converge within opts.rh_maxit. */
 int ov_rh_sign(ov_handle* h, int count, int m, const void* T, void* S, int* iters);
 
@@ -257,6 +258,7 @@ int ov_get_coefficients(const ov_handle* h, int rhs, int kcap, void* alpha, void
  *            receives sgn(T) and also holds the iterate while the call runs.
  *   iters  : HOST array of `count` ints (may be NULL): iterations used.
  *   limits : count <= 64, m <= 120, otherwise OV_ERR_TOO_LARGE; no handle needed.
+ * The inversions are in FP64 (ov_rh_sign with opts.inner_arith = OV_INNER_FP64).
  * Scratch is one fixed file-scope device array (about 31 KB per GPU that loads the
  * library, kept until exit), shared by every call: calls that overlap on the GPU race
  * on it, so serialise them (one stream, or wait between calls). The first call on a

@@ -27,7 +27,10 @@ def test_noalloc_matches_regular_entry_point_twice():
     import paper_0910_2918_gb300 as ov
 
     dims = (2, 2, 2, 2)
-    h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0)
+    # the allocation-free entry point eliminates in FP64: compare with the regular entry
+    # point in the same arithmetic
+    h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0,
+                     opts=ov.make_opts(inner_arith=ov.binding.OV_INNER_FP64))
     try:
         rng = np.random.default_rng(11)
         for count, m in ((3, 40), (2, 120)):  # two calls in a row, different shapes
