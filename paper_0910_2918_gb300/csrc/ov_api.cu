@@ -183,9 +183,10 @@ extern "C" int ov_reset_stats(ov_handle* h) {
 static int build_batch(ov_handle* h, const std::vector<int>& lat_of, int bs, Batch* b, size_t* pool) {
   const int np = (int)lat_of.size();
   std::vector<ProbDesc> d(np);
-  std::vector<int> map;
+  std::vector<int2> map;
   size_t voff = 0;
   int blk = 0;
+  bool same_lattice = true;
   for (int r = 0; r < np; ++r) {
     const Lattice& L = h->lat[lat_of[r]];
     d[r].g = L.g;
@@ -196,14 +197,24 @@ static int build_batch(ov_handle* h, const std::vector<int>& lat_of, int bs, Bat
     d[r].nblk = num_site_blocks(L.g, bs);
     voff += 12 * (size_t)L.g.V;
     blk += d[r].nblk;
-    for (int q = 0; q < d[r].nblk; ++q) map.push_back(r);
+    same_lattice = same_lattice && lat_of[r] == lat_of[0];
+  }
+  // Right-hand sides of one lattice: site-block-major order, so the blocks of every
+  // right-hand side on the same sites run together and share the links (and neighbour
+  // planes) in L2. Different lattices: problem-major.
+  if (same_lattice) {
+    for (int q = 0; q < d[0].nblk; ++q)
+      for (int r = 0; r < np; ++r) map.push_back(make_int2(r, q));
+  } else {
+    for (int r = 0; r < np; ++r)
+      for (int q = 0; q < d[r].nblk; ++q) map.push_back(make_int2(r, q));
   }
   CK(grow(h->desc, sizeof(ProbDesc) * np));
-  CK(grow(h->blkmap, sizeof(int) * map.size()));
+  CK(grow(h->blkmap, sizeof(int2) * map.size()));
   CK(cudaMemcpyAsync(h->desc.p, d.data(), sizeof(ProbDesc) * np, cudaMemcpyHostToDevice, h->st));
-  CK(cudaMemcpyAsync(h->blkmap.p, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->blkmap.p, map.data(), sizeof(int2) * map.size(), cudaMemcpyHostToDevice, h->st));
   b->desc = (const ProbDesc*)h->desc.p;
-  b->blk_prob = (const int*)h->blkmap.p;
+  b->blk_map = (const int2*)h->blkmap.p;
   b->nblocks = blk;
   b->nprob = np;
   b->block = bs;

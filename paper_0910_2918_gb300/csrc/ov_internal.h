@@ -53,7 +53,7 @@ struct ProbDesc {
 };
 struct Batch {
   const ProbDesc* desc;  // device [nprob]
-  const int* blk_prob;   // device [nblocks]: problem of each site block
+  const int2* blk_map;   // device [nblocks]: (problem, site block within the problem) of each block
   int nblocks, nprob;
   int block;             // threads per site block (64, 128 or 256)
 };

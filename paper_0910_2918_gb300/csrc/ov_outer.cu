@@ -77,12 +77,14 @@ __device__ __forceinline__ void set_step_scal(void* scal, int r, double nv, doub
 }
 
 // ------------------------------------------------------------ block reductions
-// Each thread passes its values; the block's sums go to partials[(r*nblk+bx)*4+q].
-// Returns true in the last block to finish for this right-hand side, where tot[]
-// (valid in thread 0) holds the fixed-order total over all blocks.
+// Each thread passes its values; the block's sums go to partials[(part0 + bx)*4 + q]
+// (part0: the problem's first slot, bx: the block's index within the problem, so the
+// slots do not depend on the launch order of the blocks). Returns true in the last block
+// to finish for this problem, where tot[] (valid in thread 0) holds the fixed-order total
+// over all its blocks.
 template <int NQ, int BS>
 __device__ __forceinline__ bool reduce_last(double (&v)[NQ], double* partials, unsigned* counters, int r, int part0,
-                                            int nblk, double (&tot)[NQ]) {
+                                            int bx, int nblk, double (&tot)[NQ]) {
   __shared__ double sred[BS / 32][4];
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -97,7 +99,7 @@ __device__ __forceinline__ bool reduce_last(double (&v)[NQ], double* partials, u
     for (int q = 0; q < NQ; ++q) {
       double s = 0.0;
       for (int w = 0; w < BS / 32; ++w) s += sred[w][q];
-      partials[(size_t)blockIdx.x * 4 + q] = s;
+      partials[(size_t)(part0 + bx) * 4 + q] = s;
     }
     __threadfence();
     unsigned prev = atomicAdd(&counters[r], 1u);
@@ -140,10 +142,10 @@ struct SiteRef {
 };
 template <int BS>
 __device__ __forceinline__ SiteRef site_ref(const Batch& b) {
-  const int blk = blockIdx.x;
-  const int r = __ldg(&b.blk_prob[blk]);
+  const int2 m = __ldg(&b.blk_map[blockIdx.x]);
+  const int r = m.x;
   const ProbDesc* d = &b.desc[r];
-  const int bx = blk - d->block0;
+  const int bx = m.y;
   const int s = bx * BS + threadIdx.x;
   return {r, bx, s, s < d->g.V, d};
 }
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(BS) k_pack(Batch bt, const double2* __restrict
   }
   if (!want_norm) return;
   double v[1] = {n2}, tot[1];
-  if (reduce_last<1, BS>(v, partials, counters, r, sr.d->block0, sr.d->nblk, tot) && threadIdx.x == 0) {
+  if (reduce_last<1, BS>(v, partials, counters, r, sr.d->block0, sr.bx, sr.d->nblk, tot) && threadIdx.x == 0) {
     double nrm = sqrt(tot[0]);
     size_t o = (size_t)r * c.ld + 1;
     c.nv[o] = nrm > 0.0 ? nrm : 1.0;
@@ -573,7 +575,7 @@ __global__ void __launch_bounds__(BS, step_min_blocks<P, BS>()) k_step(StepArgs 
   // warp_acc already reduced over the warp in the accumulator type; reduce_last sums
   // again over lanes, so keep only lane 0's value.
   if ((threadIdx.x & 31) != 0) { v2[0] = 0.0; v2[1] = 0.0; }
-  if (reduce_last<2, BS>(v2, a.partials, a.counters, r, d.block0, d.nblk, tot) && threadIdx.x == 0) {
+  if (reduce_last<2, BS>(v2, a.partials, a.counters, r, d.block0, sr.bx, d.nblk, tot) && threadIdx.x == 0) {
     const double ai = MODE == kModeLanczos ? 0.0 : tot[1];
     a.c.alp[co] = make_double2(tot[0], ai);
     st_scal<P>(a.scal, r, 4, tot[0], ai);
@@ -628,7 +630,7 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
   if (MODE == kModeLanczos) {
     double v1[1] = {warp_acc(nvv.re)}, tot[1];
     if (!lane0) v1[0] = 0.0;
-    if (reduce_last<1, BS>(v1, a.partials, a.counters, r, sr.d->block0, sr.d->nblk, tot) && threadIdx.x == 0) {
+    if (reduce_last<1, BS>(v1, a.partials, a.counters, r, sr.d->block0, sr.bx, sr.d->nblk, tot) && threadIdx.x == 0) {
       const double b = sqrt(tot[0]);
       const double bprev = fabs(a.c.bet[co].x);
       const size_t cn = co + 1;
@@ -647,7 +649,7 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
   } else {
     double v4[4] = {warp_acc(d.re), warp_acc(d.im), warp_acc(nvv.re), warp_acc(nww.re)}, tot[4];
     if (!lane0) { v4[0] = v4[1] = v4[2] = v4[3] = 0.0; }
-    if (reduce_last<4, BS>(v4, a.partials, a.counters, r, sr.d->block0, sr.d->nblk, tot) && threadIdx.x == 0) {
+    if (reduce_last<4, BS>(v4, a.partials, a.counters, r, sr.d->block0, sr.bx, sr.d->nblk, tot) && threadIdx.x == 0) {
       const double dre = tot[0], dim = tot[1];
       const double ad = sqrt(dre * dre + dim * dim);
       const double b = sqrt(ad);
