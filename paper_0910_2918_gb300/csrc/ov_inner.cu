@@ -484,21 +484,6 @@ struct cdf {
   df64 re, im;
 };
 
-// a + x1 y1 + x2 y2
-__device__ __forceinline__ df64 df_axpy2(df64 a, df64 x1, df64 y1, df64 x2, df64 y2) {
-  const float p1 = __fmul_rn(x1.hi, y1.hi);
-  float e1 = __fmaf_rn(x1.hi, y1.hi, -p1);
-  e1 = __fmaf_rn(x1.hi, y1.lo, e1);
-  e1 = __fmaf_rn(x1.lo, y1.hi, e1);
-  const float p2 = __fmul_rn(x2.hi, y2.hi);
-  float e2 = __fmaf_rn(x2.hi, y2.hi, -p2);
-  e2 = __fmaf_rn(x2.hi, y2.lo, e2);
-  e2 = __fmaf_rn(x2.lo, y2.hi, e2);
-  const df64 s = df_two_sum(a.hi, p1);
-  const df64 t = df_two_sum(s.hi, p2);
-  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, s.lo), t.lo), __fadd_rn(e1, e2));
-  return df_fast_two_sum(t.hi, lo);
-}
 // a + x y
 __device__ __forceinline__ df64 df_axpy1(df64 a, df64 x, df64 y) {
   const float p = __fmul_rn(x.hi, y.hi);

@@ -82,25 +82,59 @@ __device__ __forceinline__ void set_step_scal(void* scal, int r, double nv, doub
 // slots do not depend on the launch order of the blocks). Returns true in the last block
 // to finish for this problem, where tot[] (valid in thread 0) holds the fixed-order total
 // over all its blocks.
+// The block's per-warp sums (thread 0 adds them in warp order).
 template <int NQ, int BS>
-__device__ __forceinline__ bool reduce_last(double (&v)[NQ], double* partials, unsigned* counters, int r, int part0,
-                                            int bx, int nblk, double (&tot)[NQ]) {
+__device__ __forceinline__ void block_sums(const double (&v)[NQ], double (&bsum)[NQ]) {
   __shared__ double sred[BS / 32][4];
-  __shared__ int s_last;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    double w = warp_sum(v[q]);
+    const double w = warp_sum(v[q]);
     if (lane == 0) sred[warp][q] = w;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       double s = 0.0;
       for (int w = 0; w < BS / 32; ++w) s += sred[w][q];
-      partials[(size_t)(part0 + bx) * 4 + q] = s;
+      bsum[q] = s;
     }
+  }
+}
+// Double-float values: warp sums and the sum over warps stay in float pairs (float
+// pipes); thread 0 converts the block's sums to double once.
+template <int NQ, int BS>
+__device__ __forceinline__ void block_sums(const df64 (&v)[NQ], double (&bsum)[NQ]) {
+  __shared__ float2 sdf[BS / 32][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const df64 w = warp_sum(v[q]);
+    if (lane == 0) sdf[warp][q] = make_float2(w.hi, w.lo);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      df64 s = df_zero();
+      for (int w = 0; w < BS / 32; ++w) s = s + df64{sdf[w][q].x, sdf[w][q].y};
+      bsum[q] = df_to_double(s);
+    }
+  }
+}
+
+template <int NQ, int BS, class T>
+__device__ __forceinline__ bool reduce_last(T (&v)[NQ], double* partials, unsigned* counters, int r, int part0,
+                                            int bx, int nblk, double (&tot)[NQ]) {
+  __shared__ double sred[BS / 32][4];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double bsum[NQ];
+  block_sums<NQ, BS>(v, bsum);
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) partials[(size_t)(part0 + bx) * 4 + q] = bsum[q];
     __threadfence();
     unsigned prev = atomicAdd(&counters[r], 1u);
     s_last = (prev == (unsigned)(nblk - 1));
@@ -150,10 +184,6 @@ __device__ __forceinline__ SiteRef site_ref(const Batch& b) {
   return {r, bx, s, s < d->g.V, d};
 }
 
-// warp sum in the accumulator type (double-float sums stay on the float pipes; double
-// arithmetic is used only once per warp); the result is valid in every lane
-__device__ __forceinline__ double warp_acc(double a) { return warp_sum(a); }
-__device__ __forceinline__ double warp_acc(df64 a) { return df_to_double(warp_sum(a)); }
 
 // ------------------------------------------------------------ pack / unpack
 template <class P, int BS>
@@ -332,6 +362,12 @@ __device__ __forceinline__ void madd_u(dfu& acc, float u, df64 h) {
   acc.hi = s;
   acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, err));
 }
+// acc = u h, exactly as (p, e)
+__device__ __forceinline__ void set_u(dfu& acc, float u, df64 h) {
+  const float p = __fmul_rn(u, h.hi);
+  float e = __fmaf_rn(u, h.hi, -p);
+  acc = {p, __fmaf_rn(u, h.lo, e)};
+}
 __device__ __forceinline__ dfu add_u(dfu a, dfu b) {
   const float s = __fadd_rn(a.hi, b.hi);
   const float bb = __fsub_rn(s, a.hi);
@@ -398,18 +434,25 @@ __device__ __forceinline__ void hopping_df(cx<df64> (&accn)[12], const float4* _
     const int d0q = (c_dph[nu][0] + (fwd ? 2 : 0)) & 3, d1q = (c_dph[nu][1] + (fwd ? 2 : 0)) & 3;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      cxu g0 = {{0.f, 0.f}, {0.f, 0.f}}, g1 = {{0.f, 0.f}, {0.f, 0.f}};
+      cxu g0, g1;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const cx<float> ub = u[a * 3 + b];
-        // (u.re + i u.im)(h.re + i h.im)
-        madd_u(g0.re, ub.re, h0[b].re);
+        // (u.re + i u.im)(h.re + i h.im); the first product of each sum sets it
+        if (b == 0) {
+          set_u(g0.re, ub.re, h0[b].re);
+          set_u(g0.im, ub.re, h0[b].im);
+          set_u(g1.re, ub.re, h1[b].re);
+          set_u(g1.im, ub.re, h1[b].im);
+        } else {
+          madd_u(g0.re, ub.re, h0[b].re);
+          madd_u(g0.im, ub.re, h0[b].im);
+          madd_u(g1.re, ub.re, h1[b].re);
+          madd_u(g1.im, ub.re, h1[b].im);
+        }
         madd_u(g0.re, -ub.im, h0[b].im);
-        madd_u(g0.im, ub.re, h0[b].im);
         madd_u(g0.im, ub.im, h0[b].re);
-        madd_u(g1.re, ub.re, h1[b].re);
         madd_u(g1.re, -ub.im, h1[b].im);
-        madd_u(g1.im, ub.re, h1[b].im);
         madd_u(g1.im, ub.im, h1[b].re);
       }
       // U.lo row a times h.hi, into the low words
@@ -571,10 +614,8 @@ __global__ void __launch_bounds__(BS, step_min_blocks<P, BS>()) k_step(StepArgs 
       }
     }
   }
-  double v2[2] = {warp_acc(dot.re), warp_acc(dot.im)}, tot[2];
-  // warp_acc already reduced over the warp in the accumulator type; reduce_last sums
-  // again over lanes, so keep only lane 0's value.
-  if ((threadIdx.x & 31) != 0) { v2[0] = 0.0; v2[1] = 0.0; }
+  A v2[2] = {dot.re, dot.im};
+  double tot[2];
   if (reduce_last<2, BS>(v2, a.partials, a.counters, r, d.block0, sr.bx, d.nblk, tot) && threadIdx.x == 0) {
     const double ai = MODE == kModeLanczos ? 0.0 : tot[1];
     a.c.alp[co] = make_double2(tot[0], ai);
@@ -600,9 +641,9 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
   cx<A> d = {rzero<A>(), rzero<A>()};
   cx<A> nvv = {rzero<A>(), rzero<A>()}, nww = {rzero<A>(), rzero<A>()};
   if (sr.active) {
-    const V_t* pp = (const V_t*)a.p + vo + s;
-    const V_t* vc = (const V_t*)sp.vcur + vo + s;
-    V_t* tv = (V_t*)a.tv + vo + s;  // written: the stencil no longer reads it
+    const V_t* __restrict__ pp = (const V_t*)a.p + vo + s;
+    const V_t* __restrict__ vc = (const V_t*)sp.vcur + vo + s;
+    V_t* __restrict__ tv = (V_t*)a.tv + vo + s;  // written: the stencil no longer reads it
     if (MODE == kModeLanczos) {
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
@@ -611,9 +652,9 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
         acc_dot(nvv, t, t);
       }
     } else {
-      const V_t* rr = (const V_t*)a.r + vo + s;
-      const V_t* wc = (const V_t*)sp.wcur + vo + s;
-      V_t* tw = (V_t*)a.tw + vo + s;
+      const V_t* __restrict__ rr = (const V_t*)a.r + vo + s;
+      const V_t* __restrict__ wc = (const V_t*)sp.wcur + vo + s;
+      V_t* __restrict__ tw = (V_t*)a.tw + vo + s;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         const cx<R> t = ld_vec(pp + (size_t)k * g.V) - cmul(alp, ld_vec(vc + (size_t)k * g.V));
@@ -626,10 +667,9 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       }
     }
   }
-  const bool lane0 = (threadIdx.x & 31) == 0;
   if (MODE == kModeLanczos) {
-    double v1[1] = {warp_acc(nvv.re)}, tot[1];
-    if (!lane0) v1[0] = 0.0;
+    A v1[1] = {nvv.re};
+    double tot[1];
     if (reduce_last<1, BS>(v1, a.partials, a.counters, r, sr.d->block0, sr.bx, sr.d->nblk, tot) && threadIdx.x == 0) {
       const double b = sqrt(tot[0]);
       const double bprev = fabs(a.c.bet[co].x);
@@ -647,8 +687,8 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       set_step_scal<P>(a.scal, r, a.c.nv[cn], a.c.gam[cn], a.c.nw[cn], a.c.bet[cn]);
     }
   } else {
-    double v4[4] = {warp_acc(d.re), warp_acc(d.im), warp_acc(nvv.re), warp_acc(nww.re)}, tot[4];
-    if (!lane0) { v4[0] = v4[1] = v4[2] = v4[3] = 0.0; }
+    A v4[4] = {d.re, d.im, nvv.re, nww.re};
+    double tot[4];
     if (reduce_last<4, BS>(v4, a.partials, a.counters, r, sr.d->block0, sr.bx, sr.d->nblk, tot) && threadIdx.x == 0) {
       const double dre = tot[0], dim = tot[1];
       const double ad = sqrt(dre * dre + dim * dim);

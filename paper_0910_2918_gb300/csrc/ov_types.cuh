@@ -183,17 +183,42 @@ __device__ __forceinline__ df64 df_prod(float a, float b) {
   float p = __fmul_rn(a, b);
   return {p, __fmaf_rn(a, b, -p)};
 }
+// a + x1 y1 + x2 y2 in float pairs: both products exact (p = x.hi*y.hi, e = fma(x.hi, y.hi,
+// -p), cross terms folded into e), the two high words added to a.hi by TwoSum, every low
+// word summed once, one renormalisation
+__device__ __forceinline__ df64 df_axpy2(df64 a, df64 x1, df64 y1, df64 x2, df64 y2) {
+  const float p1 = __fmul_rn(x1.hi, y1.hi);
+  float e1 = __fmaf_rn(x1.hi, y1.hi, -p1);
+  e1 = __fmaf_rn(x1.hi, y1.lo, e1);
+  e1 = __fmaf_rn(x1.lo, y1.hi, e1);
+  const float p2 = __fmul_rn(x2.hi, y2.hi);
+  float e2 = __fmaf_rn(x2.hi, y2.hi, -p2);
+  e2 = __fmaf_rn(x2.hi, y2.lo, e2);
+  e2 = __fmaf_rn(x2.lo, y2.hi, e2);
+  const df64 s = df_two_sum(a.hi, p1);
+  const df64 t = df_two_sum(s.hi, p2);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, s.lo), t.lo), __fadd_rn(e1, e2));
+  return df_fast_two_sum(t.hi, lo);
+}
+// the same with float factors
+__device__ __forceinline__ df64 df_axpy2(df64 a, float x1, float y1, float x2, float y2) {
+  const float p1 = __fmul_rn(x1, y1);
+  const float e1 = __fmaf_rn(x1, y1, -p1);
+  const float p2 = __fmul_rn(x2, y2);
+  const float e2 = __fmaf_rn(x2, y2, -p2);
+  const df64 s = df_two_sum(a.hi, p1);
+  const df64 t = df_two_sum(s.hi, p2);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, s.lo), t.lo), __fadd_rn(e1, e2));
+  return df_fast_two_sum(t.hi, lo);
+}
+// acc += conj(a) b
 __device__ __forceinline__ void acc_dot(cx<df64>& acc, cx<float> a, cx<float> b) {
-  acc.re = acc.re + df_prod(a.re, b.re);
-  acc.re = acc.re + df_prod(a.im, b.im);
-  acc.im = acc.im + df_prod(a.re, b.im);
-  acc.im = acc.im + df_prod(-a.im, b.re);
+  acc.re = df_axpy2(acc.re, a.re, b.re, a.im, b.im);
+  acc.im = df_axpy2(acc.im, a.re, b.im, -a.im, b.re);
 }
 __device__ __forceinline__ void acc_dot(cx<df64>& acc, cx<df64> a, cx<df64> b) {
-  acc.re = acc.re + a.re * b.re;
-  acc.re = acc.re + a.im * b.im;
-  acc.im = acc.im + a.re * b.im;
-  acc.im = acc.im + (-a.im) * b.re;
+  acc.re = df_axpy2(acc.re, a.re, b.re, a.im, b.im);
+  acc.im = df_axpy2(acc.im, a.re, b.im, -a.im, b.re);
 }
 __device__ __forceinline__ cx<double> acc_to_double(cx<double> a) { return a; }
 __device__ __forceinline__ cx<double> acc_to_double(cx<df64> a) {
