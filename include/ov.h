@@ -110,6 +110,18 @@ typedef struct {
                            pairs on the float pipes, ~2^-48 per operation) or OV_INNER_FP64
                            [OV_INNER_DF64]; the inner Krylov vectors, coefficients and results are
                            double either way */
+  double relax;         /* DF64 handles: 0 = off; r in (0, 1]: outer steps j >= r * k_ref run their
+                           hopping sum in float arithmetic on the high words (vectors, recurrence,
+                           dot products and coefficients stay double-float). k_ref is the learned
+                           k* (ov_set_sizer) when a sizer is set, else k_fixed when set, else
+                           first_check when set; with none of them the steps stay strict. The
+                           result error grows once r * k_ref falls below the point where the
+                           remaining Krylov coefficients are ~1e-3 of the first (measured at
+                           16^4: r = 0.3 keeps 1e-8, r = 0.2 does not). Relaxation of the matvec
+                           accuracy in the late Krylov steps
+                           (inexact Krylov methods: van den Eshof and Sleijpen, SIAM J. Matrix Anal.
+                           Appl. 26 (2004)); not part of the paper's method. Both recombination
+                           modes switch at the same step [0] */
 } ov_opts;
 
 #define OV_INNER_DF64 0
@@ -130,6 +142,8 @@ typedef struct {
   long long checks;            /* stopping checks (inner evaluations) */
   long long block_size;        /* threads per site block of the last apply (autotuned or forced) */
   long long graph_launches;    /* CUDA graph replays (each counts its kernels in `launches`) */
+  long long relaxed_steps;     /* outer steps run with float hopping (opts.relax), first pass */
+  double relaxed_ms;           /* the part of stencil_ms spent in those steps (opts.timing) */
 } ov_stats;
 
 /* Per-RHS result information. */

@@ -47,7 +47,7 @@ class ov_opts(ctypes.Structure):
                 ("recombination", ctypes.c_int), ("rh_tol", ctypes.c_double), ("rh_maxit", ctypes.c_int),
                 ("breakdown_tol", ctypes.c_double), ("inner_dl", ctypes.c_int), ("k_fixed", ctypes.c_int),
                 ("check_schedule", ctypes.c_int), ("block_size", ctypes.c_int), ("graph_steps", ctypes.c_int),
-                ("timing", ctypes.c_int), ("inner_arith", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("inner_arith", ctypes.c_int), ("relax", ctypes.c_double)]
 
 
 class ov_stats(ctypes.Structure):
@@ -57,7 +57,8 @@ class ov_stats(ctypes.Structure):
                 ("update_ms", ctypes.c_double), ("inner_ms", ctypes.c_double), ("recombine_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("outer_steps", ctypes.c_longlong),
                 ("regen_steps", ctypes.c_longlong), ("checks", ctypes.c_longlong), ("block_size", ctypes.c_longlong),
-                ("graph_launches", ctypes.c_longlong)]
+                ("graph_launches", ctypes.c_longlong), ("relaxed_steps", ctypes.c_longlong),
+                ("relaxed_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

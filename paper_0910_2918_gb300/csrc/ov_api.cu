@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <climits>
 
 #include <algorithm>
 #include <map>
@@ -102,9 +103,12 @@ struct ov_handle {
   // CUDA graph of graph_steps outer steps (captured on a private stream, replayed on st)
   Buf jstate, slot_tab;
   cudaStream_t cap_st = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  StepArgs gargs{};
-  int gU = 0, gprec = -1, gmode = -1;
+  // captured graphs of U outer steps, one per step precision (strict and relaxed steps)
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    StepArgs args{};
+    int U = 0, prec = -1, mode = -1;
+  } graphs[2];
   // learned sizing
   Buf sizer_theta, sizer_feat, sizer_pred;
   int sizer_on = 0, sizer_lmin = 8, sizer_lmax = kMaxL;
@@ -117,7 +121,7 @@ struct ov_handle {
   size_t ev_used = 0;
 };
 
-enum { kClsStencil = 0, kClsUpdate = 1, kClsInner = 2, kClsRecomb = 3, kClsTotal = 4 };
+enum { kClsStencil = 0, kClsUpdate = 1, kClsInner = 2, kClsRecomb = 3, kClsTotal = 4, kClsRelaxed = 5 };
 
 // record the start event of a timed launch group (no-op unless opts.timing)
 static int tstart(ov_handle* h, int cls) {
@@ -147,6 +151,10 @@ static void tcollect(ov_handle* h) {
     if (cudaEventElapsedTime(&ms, h->ev_pool[2 * s], h->ev_pool[2 * s + 1]) != cudaSuccess) continue;
     switch (h->ev_class[s]) {
       case kClsStencil: h->stats.stencil_ms += ms; break;
+      case kClsRelaxed:
+        h->stats.stencil_ms += ms;
+        h->stats.relaxed_ms += ms;
+        break;
       case kClsUpdate: h->stats.update_ms += ms; break;
       case kClsInner: h->stats.inner_ms += ms; break;
       case kClsRecomb: h->stats.recombine_ms += ms; break;
@@ -251,6 +259,7 @@ extern "C" void ov_default_opts(ov_opts* o) {
   o->graph_steps = 8;
   o->timing = 0;
   o->inner_arith = OV_INNER_DF64;
+  o->relax = 0.0;
 }
 
 extern "C" const char* ov_strerror(int code) {
@@ -272,7 +281,8 @@ static int check_opts(const ov_opts& o) {
       o.first_check < 0 || o.recombination < 0 || o.recombination > 2 || !(o.breakdown_tol >= 0) ||
       o.check_schedule < 0 || o.check_schedule > 1 ||
       (o.block_size != 0 && o.block_size != 64 && o.block_size != 128 && o.block_size != 256) ||
-      o.graph_steps < 0 || o.graph_steps > 256 || o.inner_arith < 0 || o.inner_arith > 1)
+      o.graph_steps < 0 || o.graph_steps > 256 || o.inner_arith < 0 || o.inner_arith > 1 ||
+      !(o.relax >= 0.0 && o.relax <= 1.0))
     return OV_ERR_ARG;
   return OV_OK;
 }
@@ -395,7 +405,8 @@ extern "C" void ov_destroy(ov_handle* h) {
   for (Buf* b : all) release(*b);
   for (Buf& b : h->chunks) release(b);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (auto& gr : h->graphs)
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   release(h->jstate);
   release(h->slot_tab);
@@ -514,19 +525,23 @@ static int basis_slot(ov_handle* h, size_t pool_bytes, int slot, void** out) {
 // A graph of U outer steps for these step arguments: captured once (on a private stream;
 // the kernels take j and their slots from the device step state, so every replay runs
 // the next U steps) and kept while the arguments stay the same.
-static int graph_for(ov_handle* h, const StepArgs& a, int mode, int U) {
-  if (h->gexec && h->gU == U && h->gprec == h->prec && h->gmode == mode && memcmp(&h->gargs, &a, sizeof(a)) == 0)
+static int graph_for(ov_handle* h, const StepArgs& a, int prec, int mode, int U, cudaGraphExec_t* out) {
+  auto& gr = h->graphs[prec == kPrecDF64Relaxed ? 1 : 0];
+  *out = nullptr;
+  if (gr.exec && gr.U == U && gr.prec == prec && gr.mode == mode && memcmp(&gr.args, &a, sizeof(a)) == 0) {
+    *out = gr.exec;
     return OV_OK;
-  if (h->gexec) {
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
+  }
+  if (gr.exec) {
+    cudaGraphExecDestroy(gr.exec);
+    gr.exec = nullptr;
   }
   if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int u = 0; u < U && e == cudaSuccess; ++u) {
-    e = launch_step(h->prec, mode, a, h->cap_st);
+    e = launch_step(prec, mode, a, h->cap_st);
     if (e == cudaSuccess) e = launch_update(h->prec, mode, a, h->cap_st);
   }
   cudaError_t e2 = cudaStreamEndCapture(h->cap_st, &graph);
@@ -535,17 +550,18 @@ static int graph_for(ov_handle* h, const StepArgs& a, int mode, int U) {
     cudaGetLastError();
     return OV_ERR_CUDA;
   }
-  e = cudaGraphInstantiate(&h->gexec, graph, 0);
+  e = cudaGraphInstantiate(&gr.exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    h->gexec = nullptr;
+    gr.exec = nullptr;
     cudaGetLastError();
     return OV_ERR_CUDA;
   }
-  h->gargs = a;
-  h->gU = U;
-  h->gprec = h->prec;
-  h->gmode = mode;
+  gr.args = a;
+  gr.U = U;
+  gr.prec = prec;
+  gr.mode = mode;
+  *out = gr.exec;
   return OV_OK;
 }
 
@@ -664,6 +680,15 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   a.slot_tab = recomb == OV_RECOMB_STORED ? (void* const*)h->slot_tab.p : nullptr;
   CK(cudaMemsetAsync((char*)h->wring.p + vbn, 0, vbn, st));
   const int gU = (o.timing || o.graph_steps <= 0) ? 0 : o.graph_steps;
+  // relaxed steps (double-float handles): float hopping from step relax_from on, the
+  // same step in both passes
+  const bool relaxing = o.relax > 0.0 && h->prec == OV_PREC_DF64;
+  int relax_from = INT_MAX;
+  if (relaxing) {
+    if (o.k_fixed > 0) relax_from = std::max(1, (int)std::ceil(o.relax * o.k_fixed));
+    else if (!h->sizer_on && o.first_check > 0) relax_from = std::max(1, (int)std::ceil(o.relax * o.first_check));
+  }
+  auto step_prec = [&](int jj) { return jj >= relax_from ? kPrecDF64Relaxed : h->prec; };
   int jdone = 0;
   for (;;) {
     if (jdone >= ktarget || ndone >= nrhs) break;
@@ -733,21 +758,26 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     h->stats.block_size = a.b.block;
     // steps jn..target: whole graph units replayed, the rest launched one by one
     while (jn <= target) {
-      if (gU > 0 && target - jn + 1 >= gU) {
-        rc = graph_for(h, a, mode, gU);
-        if (rc == OV_OK && h->gexec) {
-          CK(cudaGraphLaunch(h->gexec, st));
+      const int sp = step_prec(jn);
+      // a graph unit holds steps of one precision
+      if (gU > 0 && target - jn + 1 >= gU && step_prec(jn + gU - 1) == sp) {
+        cudaGraphExec_t gx = nullptr;
+        rc = graph_for(h, a, sp, mode, gU, &gx);
+        if (rc == OV_OK && gx) {
+          CK(cudaGraphLaunch(gx, st));
           h->stats.launches += 2 * gU;
           h->stats.stencil_launches += gU;
           h->stats.update_launches += gU;
           h->stats.outer_steps += gU;
           h->stats.graph_launches += 1;
+          if (sp == kPrecDF64Relaxed) h->stats.relaxed_steps += gU;
           jn += gU;
           continue;
         }
       }
-      int ts = tstart(h, kClsStencil);
-      CK(launch_step(h->prec, mode, a, st));
+      if (sp == kPrecDF64Relaxed) h->stats.relaxed_steps += 1;
+      int ts = tstart(h, sp == kPrecDF64Relaxed ? kClsRelaxed : kClsStencil);
+      CK(launch_step(sp, mode, a, st));
       tstop(h, ts);
       ts = tstart(h, kClsUpdate);
       CK(launch_update(h->prec, mode, a, st));
@@ -797,8 +827,10 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
       }
       CK(cudaMemcpyAsync(h->cl.p, lreq.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
       if (kmax_pred > 0.0) next_check = std::max(j + 1, std::min((int)std::floor(kmax_pred), ktarget));
+      if (relaxing && kmax_pred > 0.0) relax_from = std::max(j + 1, (int)std::ceil(o.relax * kmax_pred));
       if (h->trace)
-        fprintf(stderr, "{\"ov_sizer\": %d, \"k_pred_max\": %.1f, \"l_req0\": %d}\n", j, kmax_pred, lreq[0]);
+        fprintf(stderr, "{\"ov_sizer\": %d, \"k_pred_max\": %.1f, \"l_req0\": %d, \"relax_from\": %d}\n", j,
+                kmax_pred, lreq[0], relaxing ? relax_from : -1);
     }
     const bool check = fixed ? (j == ktarget) : (j >= next_check || j == ktarget);
     if (!check) continue;
@@ -988,7 +1020,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
       b.tnext = tnxt;
       b.vprev = vprev2;
       b.vcur = vc;
-      CK(launch_step(h->prec, kModeRegen, b, st));
+      CK(launch_step(step_prec(jj), kModeRegen, b, st));
       std::swap(tcur, tnxt);
       vprev2 = vc;
     }

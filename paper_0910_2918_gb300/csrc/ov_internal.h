@@ -32,6 +32,9 @@ struct Coefs {
 
 // Modes of the stencil step kernel.
 enum StepMode { kModeLanczos = 0, kModeTwoSided = 1, kModeRegen = 2, kModeApply = 3 };
+// step precision of the relaxed double-float steps (float hopping, double-float vectors);
+// launch_step accepts it besides OV_PREC_*, every other launcher treats it as OV_PREC_DF64
+constexpr int kPrecDF64Relaxed = 3;
 
 struct Geometry {
   int V, Lx, Ly, Lz, Lt;

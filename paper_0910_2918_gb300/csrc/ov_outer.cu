@@ -27,6 +27,7 @@ template <class P> struct AccOf;
 template <> struct AccOf<PrecF64> { using A = double; using st = double2; };
 template <> struct AccOf<PrecF32> { using A = df64; using st = float4; };
 template <> struct AccOf<PrecDF64> { using A = df64; using st = float4; };
+template <> struct AccOf<PrecDF64R> { using A = df64; using st = float4; };
 
 __device__ __forceinline__ cx<double> ld_acc(const double2* p) { double2 v = *p; return {v.x, v.y}; }
 __device__ __forceinline__ cx<df64> ld_acc(const float4* p) { float4 v = *p; return {{v.x, v.y}, {v.z, v.w}}; }
@@ -275,18 +276,20 @@ __device__ __forceinline__ void hopping_df(cx<df64> (&accn)[12], const float4* _
                                            const float2* __restrict__ links, const Geometry& g, int s,
                                            const int (&xc)[4], df64 ef, df64 eb);
 
-// acc = sum over the 8 hops of the hopping term for source `src` at site s;
-// ef / eb multiply the forward / backward t hops (e^{+-mu}).
-template <class P>
-__device__ __forceinline__ void hopping(cx<typename P::R> (&acc)[12], const typename P::vec_t* __restrict__ src,
-                                        const typename P::link_t* __restrict__ links, const Geometry& g, int s,
-                                        const int (&xc)[4], typename P::R ef, typename P::R eb) {
-  using R = typename P::R;
-  using L = typename P::L;
-  if constexpr (P::id == PrecDF64::id) {
-    hopping_df(acc, src, links, g, s, xc, ef, eb);
-    return;
-  }
+// vector element for the hopping sum: as stored, or the high words of a float pair
+__device__ __forceinline__ cx<double> ld_hop(const double2* p) { return ld_vec(p); }
+__device__ __forceinline__ cx<float> ld_hop(const float2* p) { return ld_vec(p); }
+__device__ __forceinline__ cx<float> ld_hop(const float4* p) {
+  const float4 v = *p;
+  return {v.x, v.z};
+}
+
+// acc = sum over the 8 hops of the hopping term for source `src` at site s in arithmetic
+// R with links of type L; ef / eb multiply the forward / backward t hops (e^{+-mu}).
+template <class R, class L, class VT, class LT>
+__device__ __forceinline__ void hopping_plain(cx<R> (&acc)[12], const VT* __restrict__ src,
+                                              const LT* __restrict__ links, const Geometry& g, int s,
+                                              const int (&xc)[4], R ef, R eb) {
   const int V = g.V;
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
@@ -311,10 +314,10 @@ __device__ __forceinline__ void hopping(cx<typename P::R> (&acc)[12], const type
     cx<R> h0[3], h1[3];
 #pragma unroll
     for (int col = 0; col < 3; ++col) {
-      const cx<R> p0 = ld_vec(src + (size_t)(0 + col) * V + sn);
-      const cx<R> p1 = ld_vec(src + (size_t)(3 + col) * V + sn);
-      const cx<R> q0 = ld_vec(src + (size_t)(3 * b0s + col) * V + sn);
-      const cx<R> q1 = ld_vec(src + (size_t)(3 * b1s + col) * V + sn);
+      const cx<R> p0 = ld_hop(src + (size_t)(0 + col) * V + sn);
+      const cx<R> p1 = ld_hop(src + (size_t)(3 + col) * V + sn);
+      const cx<R> q0 = ld_hop(src + (size_t)(3 * b0s + col) * V + sn);
+      const cx<R> q1 = ld_hop(src + (size_t)(3 * b1s + col) * V + sn);
       h0[col] = p0 + rot(q0, b0q);
       h1[col] = p1 + rot(q1, b1q);
     }
@@ -335,6 +338,22 @@ __device__ __forceinline__ void hopping(cx<typename P::R> (&acc)[12], const type
       acc[6 + a] = acc[6 + a] + rot(d0s == 0 ? g0 : g1, d0q);
       acc[9 + a] = acc[9 + a] + rot(d1s == 0 ? g0 : g1, d1q);
     }
+  }
+}
+
+template <class P>
+__device__ __forceinline__ void hopping(cx<typename P::R> (&acc)[12], const typename P::vec_t* __restrict__ src,
+                                        const typename P::link_t* __restrict__ links, const Geometry& g, int s,
+                                        const int (&xc)[4], typename P::R ef, typename P::R eb) {
+  if constexpr (P::id == PrecDF64::id) {
+    hopping_df(acc, src, links, g, s, xc, ef, eb);
+  } else if constexpr (P::id == PrecDF64R::id) {
+    cx<float> af[12];
+    hopping_plain<float, float>(af, src, links, g, s, xc, ef.hi, eb.hi);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {{af[k].re, 0.f}, {af[k].im, 0.f}};
+  } else {
+    hopping_plain<typename P::R, typename P::L>(acc, src, links, g, s, xc, ef, eb);
   }
 }
 
@@ -512,12 +531,12 @@ __device__ __forceinline__ StepPtrs step_ptrs(const StepArgs& a) {
   return {j, vprev, vcur, wr + pb * (j & 1), wr + pb * ((j - 1) & 1)};
 }
 
-// The double-float step is capped at 128 registers a thread (16 warps an SM at every block
+// The double-float steps are capped at 128 registers a thread (16 warps an SM at every block
 // size): the hop body fits without spilling and the extra warps hide the load latency at
 // the start of each hop. The other precisions keep the compiler's choice.
 template <class P, int BS>
 constexpr int step_min_blocks() {
-  return P::id == PrecDF64::id ? 512 / BS : 1;
+  return (P::id == PrecDF64::id || P::id == PrecDF64R::id) ? 512 / BS : 1;
 }
 
 template <class P, int MODE, int BS>
@@ -825,17 +844,22 @@ cudaError_t launch_unpack(int prec, const Batch& b, const void* xi, double2* y, 
   return cudaGetLastError();
 }
 
+// steps also take kPrecDF64Relaxed (the double-float storage with float hopping)
+#define OV_STEP_DISPATCH(prec, CALL)                                \
+  if (prec == kPrecDF64Relaxed) { using P = PrecDF64R; CALL; }      \
+  else { OV_DISPATCH(prec, CALL) }
+
 cudaError_t launch_step(int prec, int mode, const StepArgs& a, cudaStream_t st) {
   const int grid = a.b.nblocks;
   switch (mode) {
     case kModeLanczos:
-      OV_BS_DISPATCH(a.b.block, OV_DISPATCH(prec, (k_step<P, kModeLanczos, BS><<<grid, BS, 0, st>>>(a))));
+      OV_BS_DISPATCH(a.b.block, OV_STEP_DISPATCH(prec, (k_step<P, kModeLanczos, BS><<<grid, BS, 0, st>>>(a))));
       break;
     case kModeTwoSided:
-      OV_BS_DISPATCH(a.b.block, OV_DISPATCH(prec, (k_step<P, kModeTwoSided, BS><<<grid, BS, 0, st>>>(a))));
+      OV_BS_DISPATCH(a.b.block, OV_STEP_DISPATCH(prec, (k_step<P, kModeTwoSided, BS><<<grid, BS, 0, st>>>(a))));
       break;
     case kModeRegen:
-      OV_BS_DISPATCH(a.b.block, OV_DISPATCH(prec, (k_step<P, kModeRegen, BS><<<grid, BS, 0, st>>>(a))));
+      OV_BS_DISPATCH(a.b.block, OV_STEP_DISPATCH(prec, (k_step<P, kModeRegen, BS><<<grid, BS, 0, st>>>(a))));
       break;
     default:
       OV_BS_DISPATCH(a.b.block, OV_DISPATCH(prec, (k_step<P, kModeApply, BS><<<grid, BS, 0, st>>>(a))));

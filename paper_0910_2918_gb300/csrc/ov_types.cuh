@@ -145,6 +145,18 @@ struct PrecDF64 {
   using link_t = float2;
   static constexpr int id = 2;
 };
+// Relaxed steps of the double-float mode: the same storage, recurrence and reductions as
+// PrecDF64, with the hopping sum in float arithmetic on the high words of the vector and
+// the links (a matvec error of a few 2^-24, admitted where the step's weight in the result
+// is small).
+struct PrecDF64R {
+  using R = df64;
+  using L = float;
+  using A = df64;
+  using vec_t = float4;
+  using link_t = float2;
+  static constexpr int id = 3;
+};
 
 __device__ __forceinline__ cx<double> ld_vec(const double2* p) {
   double2 v = *p;
