@@ -531,12 +531,18 @@ __device__ __forceinline__ StepPtrs step_ptrs(const StepArgs& a) {
   return {j, vprev, vcur, wr + pb * (j & 1), wr + pb * ((j - 1) & 1)};
 }
 
-// The double-float steps are capped at 128 registers a thread (16 warps an SM at every block
-// size): the hop body fits without spilling and the extra warps hide the load latency at
-// the start of each hop. The other precisions keep the compiler's choice.
+// Register caps of the step kernels (the warps they add hide the load latency at the start
+// of each hop; measured at 16^4 with 12 right-hand sides): 128 registers a thread for the
+// strict double-float step (16 warps an SM; its hop body fits, tighter caps spill hundreds
+// of bytes and run slower), 85 for the relaxed step (24 warps; it fits in 80: 0.50 ->
+// 0.46 ms) and 64 for the float step (32 warps, a few spilled words: 0.32 -> 0.27 ms).
+// FP64 keeps the compiler's choice.
 template <class P, int BS>
 constexpr int step_min_blocks() {
-  return (P::id == PrecDF64::id || P::id == PrecDF64R::id) ? 512 / BS : 1;
+  return P::id == PrecDF64::id    ? 512 / BS
+         : P::id == PrecDF64R::id ? 768 / BS
+         : P::id == PrecF32::id   ? 1024 / BS
+                                  : 1;
 }
 
 template <class P, int MODE, int BS>
