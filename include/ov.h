@@ -122,6 +122,12 @@ typedef struct {
                            (inexact Krylov methods: van den Eshof and Sleijpen, SIAM J. Matrix Anal.
                            Appl. 26 (2004)); not part of the paper's method. Both recombination
                            modes switch at the same step [0] */
+  int overlap_checks;   /* 1: a stopping check runs on a second, high-priority stream while up to
+                           20 further outer steps (fewer than check_interval) run speculatively;
+                           a run that stops at the check uses k = the check's step, so results
+                           are those of the serial order (not used where the previous check's
+                           largest outer estimate was within 8 tol, where a stop is likely);
+                           0: checks block the outer steps [1] */
 } ov_opts;
 
 #define OV_INNER_DF64 0

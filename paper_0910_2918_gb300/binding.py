@@ -47,7 +47,8 @@ class ov_opts(ctypes.Structure):
                 ("recombination", ctypes.c_int), ("rh_tol", ctypes.c_double), ("rh_maxit", ctypes.c_int),
                 ("breakdown_tol", ctypes.c_double), ("inner_dl", ctypes.c_int), ("k_fixed", ctypes.c_int),
                 ("check_schedule", ctypes.c_int), ("block_size", ctypes.c_int), ("graph_steps", ctypes.c_int),
-                ("timing", ctypes.c_int), ("inner_arith", ctypes.c_int), ("relax", ctypes.c_double)]
+                ("timing", ctypes.c_int), ("inner_arith", ctypes.c_int), ("relax", ctypes.c_double),
+                ("overlap_checks", ctypes.c_int)]
 
 
 class ov_stats(ctypes.Structure):

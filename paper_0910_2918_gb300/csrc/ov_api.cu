@@ -32,6 +32,8 @@ namespace {
 
 constexpr int kChunk = 64;       // outer basis slots per allocation chunk
 constexpr int kSizerSteps = 16;  // outer steps whose coefficients feed the learned sizing
+constexpr int kSpecSteps = 20;   // speculative outer steps run while a check is evaluated
+constexpr double kSpecFactor = 8.0;  // no speculation when the last estimate was within this of tol
 
 struct Buf {
   void* p = nullptr;
@@ -103,6 +105,10 @@ struct ov_handle {
   // CUDA graph of graph_steps outer steps (captured on a private stream, replayed on st)
   Buf jstate, slot_tab;
   cudaStream_t cap_st = nullptr;
+  // stopping checks overlapped with speculative outer steps: a high-priority stream and
+  // the events that order it against the handle's stream
+  cudaStream_t chk_st = nullptr;
+  cudaEvent_t ev_step = nullptr, ev_chk = nullptr;
   // captured graphs of U outer steps, one per step precision (strict and relaxed steps)
   struct Graph {
     cudaGraphExec_t exec = nullptr;
@@ -118,13 +124,14 @@ struct ov_handle {
   // event pairs recorded around timed launches: (class, start, stop)
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_class;
+  std::vector<cudaStream_t> ev_stream;
   size_t ev_used = 0;
 };
 
 enum { kClsStencil = 0, kClsUpdate = 1, kClsInner = 2, kClsRecomb = 3, kClsTotal = 4, kClsRelaxed = 5 };
 
 // record the start event of a timed launch group (no-op unless opts.timing)
-static int tstart(ov_handle* h, int cls) {
+static int tstart(ov_handle* h, int cls, cudaStream_t s = nullptr) {
   if (!h->o.timing) return -1;
   if (h->ev_used + 2 > h->ev_pool.size()) {
     for (int i = 0; i < 256; ++i) {
@@ -133,16 +140,18 @@ static int tstart(ov_handle* h, int cls) {
       h->ev_pool.push_back(e);
     }
     h->ev_class.resize(h->ev_pool.size() / 2);
+    h->ev_stream.resize(h->ev_pool.size() / 2);
   }
   const int slot = (int)(h->ev_used / 2);
   h->ev_class[slot] = cls;
-  cudaEventRecord(h->ev_pool[h->ev_used], h->st);
+  h->ev_stream[slot] = s ? s : h->st;
+  cudaEventRecord(h->ev_pool[h->ev_used], h->ev_stream[slot]);
   h->ev_used += 2;
   return slot;
 }
 static void tstop(ov_handle* h, int slot) {
   if (slot < 0) return;
-  cudaEventRecord(h->ev_pool[2 * slot + 1], h->st);
+  cudaEventRecord(h->ev_pool[2 * slot + 1], h->ev_stream[slot]);
 }
 // after the stream has drained: add the recorded durations to the statistics
 static void tcollect(ov_handle* h) {
@@ -260,6 +269,7 @@ extern "C" void ov_default_opts(ov_opts* o) {
   o->timing = 0;
   o->inner_arith = OV_INNER_DF64;
   o->relax = 0.0;
+  o->overlap_checks = 1;
 }
 
 extern "C" const char* ov_strerror(int code) {
@@ -282,7 +292,7 @@ static int check_opts(const ov_opts& o) {
       o.check_schedule < 0 || o.check_schedule > 1 ||
       (o.block_size != 0 && o.block_size != 64 && o.block_size != 128 && o.block_size != 256) ||
       o.graph_steps < 0 || o.graph_steps > 256 || o.inner_arith < 0 || o.inner_arith > 1 ||
-      !(o.relax >= 0.0 && o.relax <= 1.0))
+      !(o.relax >= 0.0 && o.relax <= 1.0) || o.overlap_checks < 0 || o.overlap_checks > 1)
     return OV_ERR_ARG;
   return OV_OK;
 }
@@ -408,6 +418,9 @@ extern "C" void ov_destroy(ov_handle* h) {
   for (auto& gr : h->graphs)
     if (gr.exec) cudaGraphExecDestroy(gr.exec);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  if (h->chk_st) cudaStreamDestroy(h->chk_st);
+  if (h->ev_step) cudaEventDestroy(h->ev_step);
+  if (h->ev_chk) cudaEventDestroy(h->ev_chk);
   release(h->jstate);
   release(h->slot_tab);
   delete h;
@@ -665,6 +678,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   std::vector<double> hk1(nrhs, 0), he1(nrhs, 0), hk2(nrhs, 0), he2(nrhs, 0);
   std::vector<int> kprev_old(nrhs, 0);
   int last_check = 0;
+  double eo_last_max = -1.0;  // largest outer estimate of the running RHS at the last check
   // device-side step state: j and the global ticket; the basis slot table; the rings
   {
     const int init[2] = {1, 0};
@@ -690,6 +704,102 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   }
   auto step_prec = [&](int jj) { return jj >= relax_from ? kPrecDF64Relaxed : h->prec; };
   int jdone = 0;
+  // outer steps jfrom+1 .. jto: basis slots (stored mode), the autotuned block size at
+  // step 1, whole graph units replayed and the rest launched one by one
+  auto run_span = [&](int jfrom, int jto) -> int {
+      // basis slots of the span (stored mode), uploaded to the device slot table
+      if (recomb == OV_RECOMB_STORED) {
+        const size_t first_new = slots.size();
+        for (int jj = jfrom + 1; jj <= jto; ++jj) {
+          void* vc = nullptr;
+          rc = basis_slot(h, vbn, jj - 1, &vc);
+          if (rc != OV_OK) {
+            if (o.recombination != OV_RECOMB_AUTO) return rc;
+            // out of memory: fall back to the double pass; the ring slot that step jj reads
+            // as v_{jj-1} gets the last stored vector
+            recomb = OV_RECOMB_TWO_PASS;
+            a.slot_tab = nullptr;
+            if (jj >= 2) CK(cudaMemcpyAsync((char*)h->vring.p + vbn * (jj & 1), slots[jj - 2], vbn,
+                                            cudaMemcpyDeviceToDevice, st));
+            break;
+          }
+          slots.push_back(vc);
+        }
+        if (slots.size() > first_new)
+          CK(cudaMemcpyAsync((void**)h->slot_tab.p + first_new, slots.data() + first_new,
+                             sizeof(void*) * (slots.size() - first_new), cudaMemcpyHostToDevice, st));
+      }
+      int jn = jfrom + 1;
+      if (jn == 1 && tune) {
+        // autotune the block size on the first step (it only reads x and the step-1
+        // scalars, so re-running it is harmless): best of two timed launches per size
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int best_bs = kBlockDefault;
+        for (int cand : {64, 128, 256}) {
+          Batch bc;
+          size_t pc = 0;
+          rc = build_batch(h, lat_of, cand, &bc, &pc);
+          if (rc != OV_OK) return rc;
+          a.b = bc;
+          float tmin = 1e30f;
+          for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaEventRecord(e0, st));
+            CK(launch_step(h->prec, mode, a, st));
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            tmin = std::min(tmin, ms);
+          }
+          h->stats.launches += 2;
+          if (tmin < best) { best = tmin; best_bs = cand; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        h->tuned[key] = best_bs;
+        rc = build_batch(h, lat_of, best_bs, &bt, &pool);
+        if (rc != OV_OK) return rc;
+        a.b = bt;
+        if (h->trace) fprintf(stderr, "{\"ov_autotune\": %d, \"ms\": %.4f}\n", best_bs, best);
+      }
+      h->stats.block_size = a.b.block;
+      // steps jn..jto: whole graph units replayed, the rest launched one by one
+      while (jn <= jto) {
+        const int sp = step_prec(jn);
+        // a graph unit holds steps of one precision
+        if (gU > 0 && jto - jn + 1 >= gU && step_prec(jn + gU - 1) == sp) {
+          cudaGraphExec_t gx = nullptr;
+          rc = graph_for(h, a, sp, mode, gU, &gx);
+          if (rc == OV_OK && gx) {
+            CK(cudaGraphLaunch(gx, st));
+            h->stats.launches += 2 * gU;
+            h->stats.stencil_launches += gU;
+            h->stats.update_launches += gU;
+            h->stats.outer_steps += gU;
+            h->stats.graph_launches += 1;
+            if (sp == kPrecDF64Relaxed) h->stats.relaxed_steps += gU;
+            jn += gU;
+            continue;
+          }
+        }
+        if (sp == kPrecDF64Relaxed) h->stats.relaxed_steps += 1;
+        int ts = tstart(h, sp == kPrecDF64Relaxed ? kClsRelaxed : kClsStencil);
+        CK(launch_step(sp, mode, a, st));
+        tstop(h, ts);
+        ts = tstart(h, kClsUpdate);
+        CK(launch_update(h->prec, mode, a, st));
+        tstop(h, ts);
+        h->stats.launches += 2;
+        h->stats.stencil_launches += 1;
+        h->stats.update_launches += 1;
+        h->stats.outer_steps += 1;
+        ++jn;
+      }
+    return OV_OK;
+  };
   for (;;) {
     if (jdone >= ktarget || ndone >= nrhs) break;
     const bool fixed_span = o.k_fixed > 0;
@@ -697,97 +807,8 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     if (h->sizer_on && !fixed_span && jdone < kSizerSteps && ktarget > kSizerSteps + 1)
       target = std::min(target, kSizerSteps);
     if (target <= jdone) target = jdone + 1;
-    // basis slots of the span (stored mode), uploaded to the device slot table
-    if (recomb == OV_RECOMB_STORED) {
-      const size_t first_new = slots.size();
-      for (int jj = jdone + 1; jj <= target; ++jj) {
-        void* vc = nullptr;
-        rc = basis_slot(h, vbn, jj - 1, &vc);
-        if (rc != OV_OK) {
-          if (o.recombination != OV_RECOMB_AUTO) return rc;
-          // out of memory: fall back to the double pass; the ring slot that step jj reads
-          // as v_{jj-1} gets the last stored vector
-          recomb = OV_RECOMB_TWO_PASS;
-          a.slot_tab = nullptr;
-          if (jj >= 2) CK(cudaMemcpyAsync((char*)h->vring.p + vbn * (jj & 1), slots[jj - 2], vbn,
-                                          cudaMemcpyDeviceToDevice, st));
-          break;
-        }
-        slots.push_back(vc);
-      }
-      if (slots.size() > first_new)
-        CK(cudaMemcpyAsync((void**)h->slot_tab.p + first_new, slots.data() + first_new,
-                           sizeof(void*) * (slots.size() - first_new), cudaMemcpyHostToDevice, st));
-    }
-    int jn = jdone + 1;
-    if (jn == 1 && tune) {
-      // autotune the block size on the first step (it only reads x and the step-1
-      // scalars, so re-running it is harmless): best of two timed launches per size
-      cudaEvent_t e0, e1;
-      CK(cudaEventCreate(&e0));
-      CK(cudaEventCreate(&e1));
-      float best = 1e30f;
-      int best_bs = kBlockDefault;
-      for (int cand : {64, 128, 256}) {
-        Batch bc;
-        size_t pc = 0;
-        rc = build_batch(h, lat_of, cand, &bc, &pc);
-        if (rc != OV_OK) return rc;
-        a.b = bc;
-        float tmin = 1e30f;
-        for (int rep = 0; rep < 2; ++rep) {
-          CK(cudaEventRecord(e0, st));
-          CK(launch_step(h->prec, mode, a, st));
-          CK(cudaEventRecord(e1, st));
-          CK(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          CK(cudaEventElapsedTime(&ms, e0, e1));
-          tmin = std::min(tmin, ms);
-        }
-        h->stats.launches += 2;
-        if (tmin < best) { best = tmin; best_bs = cand; }
-      }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      h->tuned[key] = best_bs;
-      rc = build_batch(h, lat_of, best_bs, &bt, &pool);
-      if (rc != OV_OK) return rc;
-      a.b = bt;
-      if (h->trace) fprintf(stderr, "{\"ov_autotune\": %d, \"ms\": %.4f}\n", best_bs, best);
-    }
-    h->stats.block_size = a.b.block;
-    // steps jn..target: whole graph units replayed, the rest launched one by one
-    while (jn <= target) {
-      const int sp = step_prec(jn);
-      // a graph unit holds steps of one precision
-      if (gU > 0 && target - jn + 1 >= gU && step_prec(jn + gU - 1) == sp) {
-        cudaGraphExec_t gx = nullptr;
-        rc = graph_for(h, a, sp, mode, gU, &gx);
-        if (rc == OV_OK && gx) {
-          CK(cudaGraphLaunch(gx, st));
-          h->stats.launches += 2 * gU;
-          h->stats.stencil_launches += gU;
-          h->stats.update_launches += gU;
-          h->stats.outer_steps += gU;
-          h->stats.graph_launches += 1;
-          if (sp == kPrecDF64Relaxed) h->stats.relaxed_steps += gU;
-          jn += gU;
-          continue;
-        }
-      }
-      if (sp == kPrecDF64Relaxed) h->stats.relaxed_steps += 1;
-      int ts = tstart(h, sp == kPrecDF64Relaxed ? kClsRelaxed : kClsStencil);
-      CK(launch_step(sp, mode, a, st));
-      tstop(h, ts);
-      ts = tstart(h, kClsUpdate);
-      CK(launch_update(h->prec, mode, a, st));
-      tstop(h, ts);
-      h->stats.launches += 2;
-      h->stats.stencil_launches += 1;
-      h->stats.update_launches += 1;
-      h->stats.outer_steps += 1;
-      ++jn;
-    }
+    rc = run_span(jdone, target);
+    if (rc != OV_OK) return rc;
     jdone = target;
     j = jdone;
     const bool fixed = o.k_fixed > 0;
@@ -834,32 +855,65 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     }
     const bool check = fixed ? (j == ktarget) : (j >= next_check || j == ktarget);
     if (!check) continue;
+    // the check runs on the check stream while speculative outer steps (at most
+    // kSpecSteps, never past the next check) run on the handle's stream; they only add
+    // coefficients and basis vectors beyond k = j, so the check and the result are those of
+    // the serial order, and the steps count towards the next interval if the run goes on
+    cudaStream_t cs = st;
+    int spec = 0;
+    // (not before the learned sizing has read its 16 steps: it runs where a span ends there;
+    // and not where the run is likely to stop: the previous check's largest outer estimate
+    // within kSpecFactor of tol. The choice only moves time, never the result)
+    const bool likely_stop = eo_last_max >= 0.0 && eo_last_max <= kSpecFactor * tol;
+    if (o.overlap_checks && !fixed && j < ktarget && !(h->sizer_on && j < kSizerSteps) && !likely_stop) {
+      spec = std::min(std::min(kSpecSteps, o.check_interval - 1), ktarget - j);
+      if (spec > 0) {
+        if (!h->chk_st) {
+          int lo = 0, hi = 0;
+          CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+          CK(cudaStreamCreateWithPriority(&h->chk_st, cudaStreamNonBlocking, hi));
+          CK(cudaEventCreateWithFlags(&h->ev_step, cudaEventDisableTiming));
+          CK(cudaEventCreateWithFlags(&h->ev_chk, cudaEventDisableTiming));
+        }
+        CK(cudaEventRecord(h->ev_step, st));
+        rc = run_span(j, j + spec);
+        if (rc != OV_OK) return rc;
+        CK(cudaStreamWaitEvent(h->chk_st, h->ev_step, 0));
+        cs = h->chk_st;
+      }
+    }
     // read the breakdown state first: a Lanczos breakdown fixes k for that RHS
-    CK(cudaMemcpyAsync(dstatus.data(), c.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(dkbreak.data(), c.kbreak, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(dstatus.data(), c.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(dkbreak.data(), c.kbreak, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, cs));
+    CK(cudaStreamSynchronize(cs));
+    // a breakdown recorded by a speculative step (after j) is not part of this check; one at
+    // or before j has both words written before the check began (a pair still being written
+    // by a running speculative step can show the status without its step)
+    for (int r = 0; r < nrhs; ++r)
+      if ((dstatus[r] == kStLucky || dstatus[r] == kStBreakdown) && (dkbreak[r] <= 0 || dkbreak[r] > j))
+        dstatus[r] = kStOK;
     for (int r = 0; r < nrhs; ++r) kcur[r] = (dstatus[r] != kStOK && dkbreak[r] > 0) ? std::min(dkbreak[r], j) : j;
-    CK(cudaMemcpyAsync(h->ck.p, kcur.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(h->ckprev.p, kprev.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->ck.p, kcur.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, cs));
+    CK(cudaMemcpyAsync(h->ckprev.p, kprev.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, cs));
     bool regrow = false;
     do {
     regrow = false;
     const auto tc0 = std::chrono::steady_clock::now();
-    const int ti = tstart(h, kClsInner);
+    const int ti = tstart(h, kClsInner, cs);
     cudaError_t e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, ld, iw,
                               o.rh_tol, o.rh_maxit, o.inner_dl, (double2*)h->cc_cur.p, ld, h->cacc_cur.p, h->prec,
                               (double*)h->c_est_in.p, (const double2*)h->cc_prev.p, ld, (const int*)h->ckprev.p,
-                              (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, 1, st);
+                              (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, 1, cs);
     CK(e);
     tstop(h, ti);
     h->stats.launches += 3;
     h->stats.inner_launches += 3;
     h->stats.checks += 1;
-    CK(cudaMemcpyAsync(eo.data(), h->c_est_out.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(rhst.data(), h->c_rhst.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(rhit.data(), h->c_rhit.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(leff.data(), h->ileff.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(eo.data(), h->c_est_out.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(rhst.data(), h->c_rhst.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(rhit.data(), h->c_rhit.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(leff.data(), h->ileff.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, cs));
+    CK(cudaStreamSynchronize(cs));
     // the inner estimate is needed only where the run may stop at this check
     bool want_inner = false;
     for (int r = 0; r < nrhs && !fixed; ++r)
@@ -868,18 +922,18 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
         want_inner = true;
     std::fill(ei.begin(), ei.end(), NAN);
     if (want_inner) {
-      const int t2 = tstart(h, kClsInner);
+      const int t2 = tstart(h, kClsInner, cs);
       e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, ld, iw, o.rh_tol,
                     o.rh_maxit, o.inner_dl, (double2*)h->cc_cur.p, ld, h->cacc_cur.p, h->prec,
                     (double*)h->c_est_in.p, (const double2*)h->cc_prev.p, ld, (const int*)h->ckprev.p,
-                    (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, 2, st);
+                    (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, 2, cs);
       CK(e);
       tstop(h, t2);
       h->stats.launches += 2;
       h->stats.inner_launches += 2;
-      CK(cudaMemcpyAsync(ei.data(), h->c_est_in.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(rhst.data(), h->c_rhst.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
+      CK(cudaMemcpyAsync(ei.data(), h->c_est_in.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, cs));
+      CK(cudaMemcpyAsync(rhst.data(), h->c_rhst.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, cs));
+      CK(cudaStreamSynchronize(cs));
     }
     if (h->trace) {
       const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc0).count();
@@ -942,10 +996,10 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
         estin[r] = ei[r];
         stat[r] = sr;
         CK(cudaMemcpyAsync((double2*)h->cc_fin.p + (size_t)r * ld, (double2*)h->cc_cur.p + (size_t)r * ld,
-                           sizeof(double2) * ld, cudaMemcpyDeviceToDevice, st));
+                           sizeof(double2) * ld, cudaMemcpyDeviceToDevice, cs));
         const size_t ab = acc_elem_bytes(h->prec);
         CK(cudaMemcpyAsync((char*)h->cacc_fin.p + ab * (size_t)r * ld, (char*)h->cacc_cur.p + ab * (size_t)r * ld,
-                           ab * ld, cudaMemcpyDeviceToDevice, st));
+                           ab * ld, cudaMemcpyDeviceToDevice, cs));
       } else {
         kprev[r] = kcur[r];
         // est_outer compares with the previous check, so it measures the error there;
@@ -962,8 +1016,17 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
         }
       }
     }
-    if (regrow) CK(cudaMemcpyAsync(h->cl.p, lreq.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
+    if (regrow) CK(cudaMemcpyAsync(h->cl.p, lreq.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, cs));
     } while (regrow);
+    eo_last_max = 0.0;  // an estimate without a previous check (infinite) means unknown
+    for (int r = 0; r < nrhs; ++r)
+      if (!done[r]) eo_last_max = std::max(eo_last_max, std::isnan(eo[r]) ? INFINITY : eo[r]);
+    if (cs != st) {
+      // later work on the handle's stream (the final combination) reads the check's results
+      CK(cudaEventRecord(h->ev_chk, cs));
+      CK(cudaStreamWaitEvent(st, h->ev_chk, 0));
+      jdone = j + spec;
+    }
     std::swap(h->cc_cur, h->cc_prev);
     // next check: fixed interval, or (adaptive) a jump to where the log-linear decay of
     // the error reaches tol, always followed by a partner check check_interval later

@@ -236,3 +236,23 @@ def test_adaptive_schedule_fewer_checks_same_answer(ov):
     assert s1["checks"] < s0["checks"]
     assert i1["k"] >= i0["k"]
     assert rel(y1, y0) < 5e-9
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_overlapped_checks_equal_serial_order(ov, mu):
+    """Checks overlapped with speculative outer steps give the serial result bitwise: same
+    stop, same estimates, same vector (the speculative steps only add coefficients and basis
+    vectors beyond the check's k)."""
+    dims = (8, 8, 8, 8)
+    U = oi.gauge_field(dims, "near_unit", 0, eps=0.4)
+    X = oi.point_sources_12(dims, site=9)[:4]
+    out = []
+    for ovl in (0, 1):
+        rc, y, info = gpu_sign(ov, dims, U, -1.5, mu, X, "df64", 1e-10, 800, 100, check_interval=25,
+                               first_check=100, block_size=128, overlap_checks=ovl)
+        out.append((y, info))
+    (y0, i0), (y1, i1) = out
+    assert [i["k"] for i in i0] == [i["k"] for i in i1]
+    assert [i["err_est"] for i in i0] == [i["err_est"] for i in i1]
+    assert [i["status"] for i in i1] == [0] * 4
+    assert np.array_equal(y0, y1)
