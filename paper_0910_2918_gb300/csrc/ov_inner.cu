@@ -484,15 +484,6 @@ struct cdf {
   df64 re, im;
 };
 
-// a + x y
-__device__ __forceinline__ df64 df_axpy1(df64 a, df64 x, df64 y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = __fmaf_rn(x.hi, y.hi, -p);
-  e = __fmaf_rn(x.hi, y.lo, e);
-  e = __fmaf_rn(x.lo, y.hi, e);
-  const df64 s = df_two_sum(a.hi, p);
-  return df_fast_two_sum(s.hi, __fadd_rn(__fadd_rn(a.lo, s.lo), e));
-}
 __device__ __forceinline__ df64 df_recip(df64 d) {
   const float x = __frcp_rn(d.hi);
   const df64 e = df64{1.f, 0.f} - d * x;

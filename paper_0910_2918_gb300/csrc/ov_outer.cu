@@ -34,6 +34,28 @@ __device__ __forceinline__ cx<df64> ld_acc(const float4* p) { float4 v = *p; ret
 __device__ __forceinline__ void st_acc(double2* p, cx<double> a) { *p = make_double2(a.re, a.im); }
 __device__ __forceinline__ void st_acc(float4* p, cx<df64> a) { *p = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
 
+// p - a v in one fused step per component (double-float: both products exact, one
+// renormalisation)
+template <class R> __device__ __forceinline__ cx<R> csubmul(cx<R> p, cx<R> a, cx<R> v) { return p - cmul(a, v); }
+__device__ __forceinline__ cx<df64> csubmul(cx<df64> p, cx<df64> a, cx<df64> v) {
+  return {df_axpy2(p.re, -a.re, v.re, a.im, v.im), df_axpy2(p.im, -a.re, v.im, -a.im, v.re)};
+}
+// acc += |t|^2
+__device__ __forceinline__ void acc_norm(double& acc, cx<double> t) { acc = fma(t.re, t.re, fma(t.im, t.im, acc)); }
+__device__ __forceinline__ void acc_norm(df64& acc, cx<float> t) { acc = df_axpy2(acc, t.re, t.re, t.im, t.im); }
+__device__ __forceinline__ void acc_norm(df64& acc, cx<df64> t) { acc = df_axpy2(acc, t.re, t.re, t.im, t.im); }
+// a norm that only feeds a threshold test (the serious-breakdown test of two-sided
+// Lanczos): float accumulation of the high words, double in the FP64 mode
+__device__ __forceinline__ void acc_norm_lo(double& acc, cx<double> t) { acc_norm(acc, t); }
+__device__ __forceinline__ void acc_norm_lo(float& acc, cx<float> t) { acc = fmaf(t.re, t.re, fmaf(t.im, t.im, acc)); }
+__device__ __forceinline__ void acc_norm_lo(float& acc, cx<df64> t) {
+  acc = fmaf(t.re.hi, t.re.hi, fmaf(t.im.hi, t.im.hi, acc));
+}
+template <class A> struct NormLo { using T = float; };
+template <> struct NormLo<double> { using T = double; };
+__device__ __forceinline__ double to_acc(double a, double) { return a; }
+__device__ __forceinline__ df64 to_acc(float a, df64) { return {a, 0.f}; }
+
 // accumulator += c * v  (c in accumulator type, v in vector type)
 __device__ __forceinline__ void acc_axpy(cx<double>& y, cx<double> c, cx<double> v) { y = y + cmul(c, v); }
 __device__ __forceinline__ void acc_axpy(cx<df64>& y, cx<df64> c, cx<float> v) { y = y + lcmul<df64, float>(v, c); }
@@ -510,6 +532,53 @@ __device__ __forceinline__ cx<R> g5d(int k, cx<R> psi, cx<R> hk, R mass) {
   cx<R> d = cscale(psi, mass) - chalf(hk);
   return k >= 6 ? -d : d;
 }
+__device__ __forceinline__ cx<df64> g5d(int k, cx<df64> psi, cx<df64> hk, df64 mass) {
+  const cx<df64> d = {df_axpy1(-df_half(hk.re), mass, psi.re), df_axpy1(-df_half(hk.im), mass, psi.im)};
+  return k >= 6 ? -d : d;
+}
+
+// ---- the recurrence at one site: scalars real (RS, RC) or complex -----------------------
+// In the recurrences 1/nv_j and beta_j are real, gamma_j and 1/conj(nw_j) complex: side v of
+// two-sided Lanczos scales by a real and subtracts a complex multiple, side w the reverse,
+// Lanczos has both real.
+template <bool RS, class R>
+__device__ __forceinline__ cx<R> smul(cx<R> s, cx<R> z) {
+  return RS ? cscale(z, s.re) : cmul(s, z);
+}
+template <bool RS>
+__device__ __forceinline__ cx<df64> smul(cx<df64> s, cx<df64> z) {
+  if (RS) return {z.re * s.re, z.im * s.re};
+  return {df_axpy2(df_zero(), s.re, z.re, -s.im, z.im), df_axpy2(df_zero(), s.re, z.im, s.im, z.re)};
+}
+// s q - c w
+template <bool RS, bool RC, class R>
+__device__ __forceinline__ cx<R> smulsub(cx<R> s, cx<R> q, cx<R> c, cx<R> w) {
+  return smul<RS>(s, q) - smul<RC>(c, w);
+}
+template <bool RS, bool RC>
+__device__ __forceinline__ cx<df64> smulsub(cx<df64> s, cx<df64> q, cx<df64> c, cx<df64> w) {
+  if (RS && RC) return {df_axpy2(df_zero(), s.re, q.re, -c.re, w.re), df_axpy2(df_zero(), s.re, q.im, -c.re, w.im)};
+  if (RS) return {df_axpy2(q.re * s.re, -c.re, w.re, c.im, w.im), df_axpy2(q.im * s.re, -c.re, w.im, -c.im, w.re)};
+  if (RC)
+    return {df_axpy2(-(w.re * c.re), s.re, q.re, -s.im, q.im), df_axpy2(-(w.im * c.re), s.re, q.im, s.im, q.re)};
+  return smul<false>(s, q) - smul<false>(c, w);
+}
+// v_j = scl psi and out = scl (gamma5 D psi) - cf prev at one site, 12 components; the
+// alpha partial: Lanczos v_j^dag out, two-sided side w: w_j^dag p (p from side v)
+template <bool RS, bool RC, int DOT, class R, class VT, class AT>
+__device__ __forceinline__ void step_site(const VT* src, const VT* prv, VT* cur, VT* out, const VT* pp, int V, int s,
+                                          cx<R> scl, cx<R> cf, const cx<R> (&acc)[12], R mass, cx<AT>& dot) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const cx<R> psi = ld_vec(src + (size_t)k * V + s);
+    const cx<R> cv = smul<RS>(scl, psi);
+    const cx<R> ok = smulsub<RS, RC>(scl, g5d(k, psi, acc[k], mass), cf, ld_vec(prv + (size_t)k * V));
+    st_vec(cur + (size_t)k * V, cv);
+    st_vec(out + (size_t)k * V, ok);
+    if (DOT == 1) acc_dot(dot, cv, ok);
+    if (DOT == 2) acc_dot(dot, cv, ld_vec(pp + (size_t)k * V));
+  }
+}
 
 // the step index and the step's vector slots (device-side state or host fields)
 struct StepPtrs {
@@ -627,16 +696,12 @@ __global__ void __launch_bounds__(BS, step_min_blocks<P, BS>()) k_step(StepArgs 
       V_t* cur = side == 0 ? (V_t*)sp.vcur + vo + s : (V_t*)sp.wcur + vo + s;
       V_t* out = side == 0 ? (V_t*)a.p + vo + s : (V_t*)a.r + vo + s;
       const V_t* pp = (const V_t*)a.p + vo + s;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        const cx<R> psi = ld_vec(src + (size_t)k * g.V + s);
-        const cx<R> cv = cmul(scl, psi);
-        const cx<R> ok = cmul(scl, g5d(k, psi, acc[k], mass)) - cmul(cf, ld_vec(prv + (size_t)k * g.V));
-        st_vec(cur + (size_t)k * g.V, cv);
-        st_vec(out + (size_t)k * g.V, ok);
-        if (MODE == kModeLanczos) acc_dot(dot, cv, ok);
-        else if (side == 1) acc_dot(dot, cv, ld_vec(pp + (size_t)k * g.V));
-      }
+      if (MODE == kModeLanczos)
+        step_site<true, true, 1>(src, prv, cur, out, pp, g.V, s, scl, cf, acc, mass, dot);
+      else if (side == 0)
+        step_site<true, false, 0>(src, prv, cur, out, pp, g.V, s, scl, cf, acc, mass, dot);
+      else
+        step_site<false, true, 2>(src, prv, cur, out, pp, g.V, s, scl, cf, acc, mass, dot);
     }
   }
   A v2[2] = {dot.re, dot.im};
@@ -663,8 +728,10 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
   const size_t co = (size_t)r * a.c.ld + sp.j;
   const cx<R> alp = ld_scal<P>(a.scal, r, 4);
   const cx<R> calp = ld_scal<P>(a.scal, r, 5);
+  using NL = typename NormLo<A>::T;
   cx<A> d = {rzero<A>(), rzero<A>()};
-  cx<A> nvv = {rzero<A>(), rzero<A>()}, nww = {rzero<A>(), rzero<A>()};
+  A nvv = rzero<A>();              // ||v~||^2: beta in Lanczos
+  NL nvl = NL(0), nwl = NL(0);     // ||v~||^2, ||w~||^2 for the breakdown test of 2sL
   if (sr.active) {
     const V_t* __restrict__ pp = (const V_t*)a.p + vo + s;
     const V_t* __restrict__ vc = (const V_t*)sp.vcur + vo + s;
@@ -672,9 +739,9 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
     if (MODE == kModeLanczos) {
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        const cx<R> t = ld_vec(pp + (size_t)k * g.V) - cmul(alp, ld_vec(vc + (size_t)k * g.V));
+        const cx<R> t = csubmul(ld_vec(pp + (size_t)k * g.V), alp, ld_vec(vc + (size_t)k * g.V));
         st_vec(tv + (size_t)k * g.V, t);
-        acc_dot(nvv, t, t);
+        acc_norm(nvv, t);
       }
     } else {
       const V_t* __restrict__ rr = (const V_t*)a.r + vo + s;
@@ -682,18 +749,18 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       V_t* __restrict__ tw = (V_t*)a.tw + vo + s;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        const cx<R> t = ld_vec(pp + (size_t)k * g.V) - cmul(alp, ld_vec(vc + (size_t)k * g.V));
-        const cx<R> u = ld_vec(rr + (size_t)k * g.V) - cmul(calp, ld_vec(wc + (size_t)k * g.V));
+        const cx<R> t = csubmul(ld_vec(pp + (size_t)k * g.V), alp, ld_vec(vc + (size_t)k * g.V));
+        const cx<R> u = csubmul(ld_vec(rr + (size_t)k * g.V), calp, ld_vec(wc + (size_t)k * g.V));
         st_vec(tv + (size_t)k * g.V, t);
         st_vec(tw + (size_t)k * g.V, u);
         acc_dot(d, u, t);
-        acc_dot(nvv, t, t);
-        acc_dot(nww, u, u);
+        acc_norm_lo(nvl, t);
+        acc_norm_lo(nwl, u);
       }
     }
   }
   if (MODE == kModeLanczos) {
-    A v1[1] = {nvv.re};
+    A v1[1] = {nvv};
     double tot[1];
     if (reduce_last<1, BS>(v1, a.partials, a.counters, r, sr.d->block0, sr.bx, sr.d->nblk, tot) && threadIdx.x == 0) {
       const double b = sqrt(tot[0]);
@@ -712,7 +779,7 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       set_step_scal<P>(a.scal, r, a.c.nv[cn], a.c.gam[cn], a.c.nw[cn], a.c.bet[cn]);
     }
   } else {
-    A v4[4] = {d.re, d.im, nvv.re, nww.re};
+    A v4[4] = {d.re, d.im, to_acc(nvl, A()), to_acc(nwl, A())};
     double tot[4];
     if (reduce_last<4, BS>(v4, a.partials, a.counters, r, sr.d->block0, sr.bx, sr.d->nblk, tot) && threadIdx.x == 0) {
       const double dre = tot[0], dim = tot[1];

@@ -212,6 +212,15 @@ __device__ __forceinline__ df64 df_axpy2(df64 a, df64 x1, df64 y1, df64 x2, df64
   const float lo = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, s.lo), t.lo), __fadd_rn(e1, e2));
   return df_fast_two_sum(t.hi, lo);
 }
+// a + x y
+__device__ __forceinline__ df64 df_axpy1(df64 a, df64 x, df64 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const df64 s = df_two_sum(a.hi, p);
+  return df_fast_two_sum(s.hi, __fadd_rn(__fadd_rn(a.lo, s.lo), e));
+}
 // the same with float factors
 __device__ __forceinline__ df64 df_axpy2(df64 a, float x1, float y1, float x2, float y2) {
   const float p1 = __fmul_rn(x1, y1);
