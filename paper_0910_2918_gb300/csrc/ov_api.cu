@@ -847,8 +847,12 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
         lreq[r] = std::max(h->sizer_lmin, std::min(lr, std::min(h->sizer_lmax, std::min(l, kMaxL))));
       }
       CK(cudaMemcpyAsync(h->cl.p, lreq.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
-      if (kmax_pred > 0.0) next_check = std::max(j + 1, std::min((int)std::floor(kmax_pred), ktarget));
-      if (relaxing && kmax_pred > 0.0) relax_from = std::max(j + 1, (int)std::ceil(o.relax * kmax_pred));
+      // (at most one interval before k_max, so that the check at k_max has a baseline)
+      if (kmax_pred > 0.0)
+        next_check = std::max(j + 1, std::min((int)std::floor(std::min(kmax_pred, (double)ktarget)),
+                                              ktarget - o.check_interval));
+      if (relaxing && kmax_pred > 0.0)
+        relax_from = std::max(j + 1, (int)std::ceil(o.relax * std::min(kmax_pred, (double)ktarget)));
       if (h->trace)
         fprintf(stderr, "{\"ov_sizer\": %d, \"k_pred_max\": %.1f, \"l_req0\": %d, \"relax_from\": %d}\n", j,
                 kmax_pred, lreq[0], relaxing ? relax_from : -1);
