@@ -170,3 +170,18 @@ def test_learned_sizing_at_24c48_two_pass(ov):
         assert err < 1e-7, (sized, err)
     assert res[1][2]["checks"] < res[0][2]["checks"]
     assert res[1][3] < res[0][3]
+
+
+def test_prediction_beyond_k_max_keeps_a_final_baseline(ov):
+    """A predicted k* beyond k_max puts the first check one interval before k_max, so the
+    check at k_max has a baseline estimate and converged runs report OK."""
+    dims = (6, 6, 6, 6)
+    U = oi.gauge_field(dims, "near_unit", 0, eps=0.3)
+    x = oi.gaussian_source(dims, 1).reshape(1, -1)
+    y = np.zeros_like(x)
+    with ov.Overlap(dims, U, -1.6, 0.2, "fp64", opts=ov.make_opts(check_interval=10)) as op:
+        op.set_sizer(_constant_predictor(5000.0, 80.0), 8, 120)
+        rc, info = op.sign_apply(x, y, 1e-9, 600, 120)
+        st = op.stats()
+    assert rc == 0 and info[0]["status"] == 0 and info[0]["err_est"] <= 1e-9
+    assert info[0]["k"] == 600 and st["checks"] >= 2
