@@ -904,10 +904,13 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     regrow = false;
     const auto tc0 = std::chrono::steady_clock::now();
     const int ti = tstart(h, kClsInner, cs);
+    // where a stop is likely, both Roberts-Higham sets (the inner estimate's too) in one
+    // launch instead of a second round trip
+    const int phase = (likely_stop && !fixed) ? 0 : 1;
     cudaError_t e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, ld, iw,
                               o.rh_tol, o.rh_maxit, o.inner_dl, (double2*)h->cc_cur.p, ld, h->cacc_cur.p, h->prec,
                               (double*)h->c_est_in.p, (const double2*)h->cc_prev.p, ld, (const int*)h->ckprev.p,
-                              (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, 1, cs);
+                              (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, phase, cs);
     CK(e);
     tstop(h, ti);
     h->stats.launches += 3;
@@ -925,7 +928,10 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
           (eo[r] <= tol || dstatus[r] == kStLucky || j == ktarget))
         want_inner = true;
     std::fill(ei.begin(), ei.end(), NAN);
-    if (want_inner) {
+    if (want_inner && phase == 0) {
+      CK(cudaMemcpyAsync(ei.data(), h->c_est_in.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, cs));
+      CK(cudaStreamSynchronize(cs));
+    } else if (want_inner) {
       const int t2 = tstart(h, kClsInner, cs);
       e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, ld, iw, o.rh_tol,
                     o.rh_maxit, o.inner_dl, (double2*)h->cc_cur.p, ld, h->cacc_cur.p, h->prec,
