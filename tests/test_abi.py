@@ -68,3 +68,43 @@ def test_no_cpu_fallback_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_default_options_match_the_header(libov):
+    """The defaults ov_default_opts fills are the ones include/ov.h documents in brackets."""
+    import paper_0910_2918_gb300 as ov
+
+    o = ov.ov_default_opts()
+    assert (o.first_check, o.recombination, o.k_fixed, o.check_schedule, o.block_size, o.graph_steps,
+            o.timing) == (0, 2, 0, 0, 0, 8, 0)
+    assert o.rh_tol == 1e-10 and o.breakdown_tol == 1e-14
+    assert o.inner_arith == ov.binding.OV_INNER_DF64 and o.relax == 0.0 and o.overlap_checks == 1
+    hdr = open(os.path.join(ROOT, "include", "ov.h")).read()
+    for name, default in (("inner_arith", "[OV_INNER_DF64]"), ("overlap_checks", "[1]"), ("graph_steps", "[8]")):
+        block = hdr[hdr.index("int " + name + ";"):]
+        assert default in block[:block.index("*/")], name
+
+
+def test_options_struct_layout_matches_the_header(libov):
+    """The binding's ctypes mirror has the header's fields in the header's order."""
+    import paper_0910_2918_gb300 as ov
+
+    hdr = open(os.path.join(ROOT, "include", "ov.h")).read()
+    body = hdr[hdr.index("typedef struct {\n  int check_interval;"):]
+    body = body[:body.index("} ov_opts;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(?:int|double)\s+([a-z_]+)\s*;", body)
+    assert fields == [f for f, _ in ov.binding.ov_opts._fields_]
+
+
+@pytest.mark.parametrize("struct", ["ov_stats", "ov_info", "ov_geom"])
+def test_result_struct_layouts_match_the_header(libov, struct):
+    import paper_0910_2918_gb300 as ov
+
+    hdr = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "ov.h")).read(), flags=re.S)
+    end = hdr.index("} " + struct + ";")
+    body = hdr[hdr.rindex("typedef struct {", 0, end):end]
+    fields = []
+    for decl in re.findall(r"\b(?:int|double|long long)\s+([^;]+);", body):
+        fields += [f.strip().split("[")[0] for f in decl.split(",")]
+    assert fields == [f for f, _ in getattr(ov.binding, struct)._fields_]
