@@ -92,6 +92,20 @@ def profile_traffic(path=PROFILE):
     return float(t.group(1))
 
 
+def profile_inst(path):
+    """warp instructions per launch of the profiled step kernel from the committed ncu
+    summary, if the kernel source still has the hash the counters were taken with."""
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"k_step<[^|]*\n(?:.*\n)*?\| warp instructions \(`smsp__inst_executed.sum`\) \| ([0-9.]+)", txt)
+    if not m or not t or m.group(1) != kernel_hash():
+        return None
+    return float(t.group(1))
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -371,6 +385,7 @@ def run_ours(args, rank, world, local_rank):
     # and relaxed); algorithmic bytes per launch: 8 spinor passes of 16-byte complex per site
     # and RHS plus the links once (float pairs strict, high words relaxed)
     V = int(np.prod(DIMS))
+    clk_summary = clk.summary()
     kernels = []
     n_rel, ms_rel = st["relaxed_steps"], st["relaxed_ms"]
     n_str, ms_str = st["stencil_launches"] - n_rel, st["stencil_ms"] - ms_rel
@@ -383,9 +398,16 @@ def run_ours(args, rank, world, local_rank):
             continue
         ab = V * (NRHS * 8 * 12 * 16 + lb)
         avg = ms_k / n_k
+        # instruction issue: 152 SMs x 4 schedulers x 1 warp instruction per clock
+        wi = profile_inst(prof)
+        sm_hz = (clk_summary.get("sm_mhz") or 2070.0) * 1e6
+        issue = None if wi is None else {
+            "warp_inst_per_launch": wi, "achieved_ginst_s": wi / (avg * 1e-3) / 1e9,
+            "peak_ginst_s": 152 * 4 * sm_hz / 1e9, "frac": wi / (avg * 1e-3) / (152 * 4 * sm_hz),
+            "source": "ncu smsp__inst_executed.sum of the committed profile / live launch time"}
         kernels.append({"kernel": name, "launches_per_step": n_k / args.steps, "total_ms_per_step": ms_k / args.steps,
                         "alg_bytes_per_launch": ab, "avg_launch_ms": avg, "achieved_gbs": ab / (avg * 1e-3) / 1e9,
-                        "traffic": profile_traffic(prof)})
+                        "traffic": profile_traffic(prof), "issue": issue})
     dom = max(kernels, key=lambda q: q["total_ms_per_step"])
     alg_bytes, st_ms, achieved, traffic = dom["alg_bytes_per_launch"], dom["avg_launch_ms"], dom["achieved_gbs"], \
         dom["traffic"]
@@ -440,7 +462,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": world * NRHS * args.steps / (e2e_ms * 1e-3) * (good_e2e_all / (world * NRHS * args.steps)),
                 "unit": "applies/s", "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(X.nbytes)},
         "gpu_launches": int(st["launches"]),
-        "clocks": clk.summary(),
+        "clocks": clk_summary,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
