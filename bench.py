@@ -106,6 +106,34 @@ def profile_inst(path):
     return float(t.group(1))
 
 
+# ------------------------------------------------------------------ replicas
+def rank_max(dist, vals, device):
+    """The maximum over ranks of each value (the slowest replica's time); one process when
+    dist is None."""
+    import torch
+
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def rank_sum(dist, vals, device):
+    """The sum over ranks of each value (applies every replica finished within the bar)."""
+    import torch
+
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t]
+
+
+def whole_job(good_all, ms_max):
+    """Whole-job throughput: the applies of all replicas that met the bar over the slowest
+    replica's time."""
+    return good_all / (ms_max * 1e-3)
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -276,10 +304,7 @@ def run_ours(args, rank, world, local_rank):
     ms_strict = e0.elapsed_time(e1)
     st_strict = op.stats()
     op.set_opts(relax=RELAX, **hkw)
-    tmax = torch.tensor([ms, t_e2e * 1e3, ms_strict], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max, e2e_ms, ms_strict_max = float(tmax[0]), float(tmax[1]), float(tmax[2])
+    ms_max, e2e_ms, ms_strict_max = rank_max(dist, [ms, t_e2e * 1e3, ms_strict], "cuda")
     # the float (mixed-precision) stencil on the same workload: HBM fraction of its fused
     # two-sided step (k fixed, outside the timed region)
     fp32_stencil = None
@@ -365,10 +390,7 @@ def run_ours(args, rank, world, local_rank):
         good_e2e = good
         good_strict = args.steps * sum(1 for i in info_s if i["status"] == 0 and i["err_est"] <= TOL)
         errs_strict = None
-    gsum = torch.tensor([good, good_e2e, good_strict], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(gsum, op=dist.ReduceOp.SUM)
-    good_all, good_e2e_all, good_strict_all = float(gsum[0]), float(gsum[1]), float(gsum[2])
+    good_all, good_e2e_all, good_strict_all = rank_sum(dist, [good, good_e2e, good_strict], "cuda")
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -411,7 +433,6 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kernels, key=lambda q: q["total_ms_per_step"])
     alg_bytes, st_ms, achieved, traffic = dom["alg_bytes_per_launch"], dom["avg_launch_ms"], dom["achieved_gbs"], \
         dom["traffic"]
-    value = world * NRHS * args.steps / (ms_max * 1e-3)
     good_frac = good_all / (world * NRHS * args.steps)
     cpu = None
     if not args.no_cpu:
@@ -420,7 +441,7 @@ def run_ours(args, rank, world, local_rank):
                "seconds": round(spent, 1)}
     line = {
         "metric": METRIC,
-        "value": value * good_frac,
+        "value": whole_job(good_all, ms_max),
         "unit": "applies/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -442,8 +463,7 @@ def run_ours(args, rank, world, local_rank):
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": st_ms, "peak_source": peak_src,
                      "block_size": st["block_size"]},
         "step_kernels": [dict(q, frac=q["achieved_gbs"] / hbm) for q in kernels],
-        "strict_df64": {"applies_per_s": world * NRHS * args.steps / (ms_strict_max * 1e-3)
-                        * (good_strict_all / (world * NRHS * args.steps)),
+        "strict_df64": {"applies_per_s": whole_job(good_strict_all, ms_strict_max),
                         "ms_per_step": ms_strict_max / args.steps, "k_used": max(i["k"] for i in info_s),
                         "applies_within_tol": good_strict_all / (world * NRHS * args.steps),
                         "rel_err_vs_fp64_path_max": max(errs_strict) if errs_strict else None,
@@ -457,9 +477,9 @@ def run_ours(args, rank, world, local_rank):
         "stencil_fp32": fp32_stencil,
         "mixed_fp32": mixed,
         "plain_fp64_nested": plain,
-        "speedup_vs_plain_fp64": (value * good_frac / plain["applies_per_s"]) if plain else None,
+        "speedup_vs_plain_fp64": (whole_job(good_all, ms_max) / plain["applies_per_s"]) if plain else None,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * NRHS * args.steps / (e2e_ms * 1e-3) * (good_e2e_all / (world * NRHS * args.steps)),
+        "e2e": {"value": whole_job(good_e2e_all, e2e_ms),
                 "unit": "applies/s", "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(X.nbytes)},
         "gpu_launches": int(st["launches"]),
         "clocks": clk_summary,
