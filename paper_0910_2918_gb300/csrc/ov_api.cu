@@ -9,7 +9,11 @@
 //       and the stopping estimates
 //   recombination y = ||x|| V_k c from the stored basis, or by regenerating v_j from
 //   the stored coefficients in a second pass (double pass, Sec. 4).
-// The only device->host traffic inside the loop is the per-check status readback.
+// The only device->host traffic inside the loop is the per-check readback. Runs of steps
+// between checks replay captured CUDA graphs; a check runs on a second, high-priority
+// stream while speculative steps continue (results as in the serial order); with learned
+// sizing the first check goes to the predicted k*; with opts.relax the late steps use
+// float hopping (both passes switch at the same step).
 #include <math.h>
 #include <stdio.h>
 

@@ -5,7 +5,12 @@
 // Layout: an internal spinor field is [rhs][12][V] of the precision's storage type
 // (component c = 3*spin + colour, site fastest), so a warp reads consecutive sites of
 // one component (coalesced). Links are [4][9][V] (nu, a*3+b, site) with the
-// antiperiodic t-boundary sign folded into U_t on the last time slice.
+// antiperiodic t-boundary sign folded into U_t on the last time slice; the double-float
+// mode keeps a second plane of low words 36 V elements further on.
+//
+// Precisions: FP64; FP32 (float vectors and links, double-float reductions); double-float
+// (vectors and links as float pairs, compensated hop sums); and the relaxed double-float
+// steps (the same storage and recurrence with the hop sum in float on the high words).
 //
 // Reductions: every block writes its partial sums (double) to a partials array; the
 // last block of each right-hand side (atomic ticket, no spin-wait) adds the partials in
