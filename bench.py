@@ -72,9 +72,14 @@ def make_inputs():
 
 
 def kernel_hash():
+    """Hash of the stencil sources without comments and blank lines (a profile stays valid
+    while the code it was captured on is unchanged)."""
     h = hashlib.sha256()
     for f in STENCIL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        src = open(os.path.join(ROOT, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        lines = [ln.split("//")[0].rstrip() for ln in src.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 
