@@ -68,3 +68,19 @@ def test_reference_arm_runs_on_rank_zero_only():
 
     args = argparse.Namespace(steps=1, warmup=0, cpu_seconds=1.0)
     assert bench.run_reference(args, rank=1, world=2) is None
+
+
+def test_profile_summaries_parse():
+    """bench.py reads the DRAM traffic and instruction counts of the step kernels from the
+    committed ncu summaries (and uses them only while the kernel source hash matches)."""
+    sys.path.insert(0, ROOT)
+    import re
+
+    import bench
+
+    for path in (bench.PROFILE, bench.PROFILE_RELAXED):
+        txt = open(path).read()
+        assert re.search(r"kernel_source_hash:\s*[0-9a-f]{16}", txt)
+        assert re.search(r"dram_bytes_per_launch_full_size:\s*[0-9.eE+]+", txt)
+        assert "smsp__inst_executed.sum" in txt
+    assert len(bench.kernel_hash()) == 16
