@@ -287,6 +287,15 @@ template <class R> __device__ __forceinline__ cx<R> rot(cx<R> z, int q) {
   cx<R> r = {sw ? z.im : z.re, sw ? z.re : z.im};
   return {rneg(r.re, q == 1 || q == 2), rneg(r.im, q >= 2)};
 }
+// cos(q pi/2), sin(q pi/2) and z + i^q w with them (see hopping_plain)
+template <class R> __device__ __forceinline__ R phase_c(int q) { return R((q == 0) - (q == 2)); }
+template <class R> __device__ __forceinline__ R phase_s(int q) { return R((q == 1) - (q == 3)); }
+__device__ __forceinline__ cx<float> add_rot(cx<float> z, cx<float> w, float c, float s) {
+  return {__fmaf_rn(-s, w.im, __fmaf_rn(c, w.re, z.re)), __fmaf_rn(s, w.re, __fmaf_rn(c, w.im, z.im))};
+}
+__device__ __forceinline__ cx<double> add_rot(cx<double> z, cx<double> w, double c, double s) {
+  return {__fma_rn(-s, w.im, __fma_rn(c, w.re, z.re)), __fma_rn(s, w.re, __fma_rn(c, w.im, z.im))};
+}
 __device__ __forceinline__ cx<double> lconj(cx<double> u, bool c) { return {u.re, c ? -u.im : u.im}; }
 __device__ __forceinline__ cx<float> lconj(cx<float> u, bool c) { return {u.re, c ? -u.im : u.im}; }
 
@@ -338,6 +347,10 @@ __device__ __forceinline__ void hopping_plain(cx<R> (&acc)[12], const VT* __rest
     }
     const int b0s = c_bsrc[nu][0], b1s = c_bsrc[nu][1];
     const int b0q = (c_bph[nu][0] + (fwd ? 2 : 0)) & 3, b1q = (c_bph[nu][1] + (fwd ? 2 : 0)) & 3;
+    // i^q as (c, s) in {0, +-1}: z + i^q w = (z.re + c w.re - s w.im, z.im + c w.im + s w.re)
+    // by fused multiply-adds; one of c, s is zero, so each component is rounded once, as a
+    // plain addition of the rotated term would be
+    const R c0 = phase_c<R>(b0q), s0 = phase_s<R>(b0q), c1 = phase_c<R>(b1q), s1 = phase_s<R>(b1q);
     cx<R> h0[3], h1[3];
 #pragma unroll
     for (int col = 0; col < 3; ++col) {
@@ -345,13 +358,14 @@ __device__ __forceinline__ void hopping_plain(cx<R> (&acc)[12], const VT* __rest
       const cx<R> p1 = ld_hop(src + (size_t)(3 + col) * V + sn);
       const cx<R> q0 = ld_hop(src + (size_t)(3 * b0s + col) * V + sn);
       const cx<R> q1 = ld_hop(src + (size_t)(3 * b1s + col) * V + sn);
-      h0[col] = p0 + rot(q0, b0q);
-      h1[col] = p1 + rot(q1, b1q);
+      h0[col] = add_rot(p0, q0, c0, s0);
+      h1[col] = add_rot(p1, q1, c1, s1);
     }
     const bool sc = nu == 3;
     const R fac = fwd ? ef : eb;
     const int d0s = c_dsrc[nu][0], d1s = c_dsrc[nu][1];
     const int d0q = (c_dph[nu][0] + (fwd ? 2 : 0)) & 3, d1q = (c_dph[nu][1] + (fwd ? 2 : 0)) & 3;
+    const R e0 = phase_c<R>(d0q), f0 = phase_s<R>(d0q), e1 = phase_c<R>(d1q), f1 = phase_s<R>(d1q);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       cx<R> g0 = lcmul<R, L>(u[a * 3 + 0], h0[0]) + lcmul<R, L>(u[a * 3 + 1], h0[1]) + lcmul<R, L>(u[a * 3 + 2], h0[2]);
@@ -362,8 +376,8 @@ __device__ __forceinline__ void hopping_plain(cx<R> (&acc)[12], const VT* __rest
       }
       acc[0 + a] = acc[0 + a] + g0;
       acc[3 + a] = acc[3 + a] + g1;
-      acc[6 + a] = acc[6 + a] + rot(d0s == 0 ? g0 : g1, d0q);
-      acc[9 + a] = acc[9 + a] + rot(d1s == 0 ? g0 : g1, d1q);
+      acc[6 + a] = add_rot(acc[6 + a], d0s == 0 ? g0 : g1, e0, f0);
+      acc[9 + a] = add_rot(acc[9 + a], d1s == 0 ? g0 : g1, e1, f1);
     }
   }
 }
