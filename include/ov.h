@@ -114,11 +114,10 @@ typedef struct {
                            hopping sum in float arithmetic on the high words (vectors, recurrence,
                            dot products and coefficients stay double-float). k_ref is the learned
                            k* (ov_set_sizer) when a sizer is set, else k_fixed when set, else
-                           first_check when set; with none of them the steps stay strict. The
-                           result error grows once r * k_ref falls below the point where the
-                           remaining Krylov coefficients are ~1e-3 of the first (measured at
-                           16^4: r = 0.3 keeps 1e-8, r = 0.2 does not). Relaxation of the matvec
-                           accuracy in the late Krylov steps
+                           first_check when set; with none of them the steps stay strict. Too
+                           early a switch shows in the result (measured at 16^4 with the learned
+                           k*: r = 0.3 keeps every error within 1e-8, r = 0.2 does not).
+                           Relaxation of the matvec accuracy in the late Krylov steps
                            (inexact Krylov methods: van den Eshof and Sleijpen, SIAM J. Matrix Anal.
                            Appl. 26 (2004)); not part of the paper's method. Both recombination
                            modes switch at the same step [0] */
