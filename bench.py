@@ -42,6 +42,9 @@ TOL, K_MAX, L_INNER = 1e-8, 1000, 72
 # against the double-precision path: only applies with a measured error <= TOL count
 TOL_STOP = 5e-9
 TOL_MIXED, MIXED_STOP, MIXED_REPS = 1e-6, 5e-7, 3
+# the 48-lattice float batch: its Haar lattices converge slowly, where the estimate (the change
+# of c over 25 steps) undershoots the error by up to ~4x, so it stops 10x below its 1e-6 bar
+BATCH_FP32_STOP = 1e-7
 L_MAX = 120
 NRHS = 12
 PREC = "df64"
@@ -49,6 +52,9 @@ CHECK_FIRST, CHECK_EVERY = 100, 25
 STENCIL_SOURCES = ["paper_0910_2918_gb300/csrc/ov_outer.cu", "paper_0910_2918_gb300/csrc/ov_types.cuh"]
 PROFILE = os.path.join(ROOT, "profiles", "stencil_twosided_df64_16x16x16x16_12rhs.md")
 PROFILE_RELAXED = os.path.join(ROOT, "profiles", "stencil_twosided_relaxed_16x16x16x16_12rhs.md")
+# oracle answers at 16^4 for two of the point sources (written by tests/golden/make_golden.py,
+# which calls only the oracle): samples of y, ||y||, projections and the oracle's stopping step
+GOLDEN = os.path.join(ROOT, "tests", "golden", "c3_16x16x16x16_mu0.2_sign.json")
 # mixed form of the headline: outer steps from RELAX x (learned k*) on run the hopping sum in
 # float (vectors, recurrence, reductions and coefficients stay double-float)
 RELAX = 0.4
@@ -197,47 +203,175 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(U, x, k_used, l_used, seconds_target=15.0):
-    """Time the oracle on a bounded sample of one right-hand side: outer two-sided
-    Lanczos steps until ~seconds_target, plus one inner level at the GPU's k; return
-    (applies/s extrapolated to k_used outer steps and k_used/CHECK_EVERY checks,
-    description)."""
+def golden():
+    try:
+        return json.load(open(GOLDEN))
+    except OSError:
+        return None
+
+
+def oracle_k_stop(default=333):
+    """Where the oracle's own stopping rule stops on this workload at the benchmark's
+    tolerance and check schedule (largest over the stored sources), else `default`."""
+    g = golden()
+    try:
+        ks = [s["k_stop_l72_check100_25"][f"{TOL_STOP:g}"] for s in g["sources"].values()]
+        return int(max(ks)), "oracle stopping rule (stored oracle coefficients, tests/golden)"
+    except (TypeError, KeyError, ValueError):
+        return default, "assumed"
+
+
+def _time_outer(U, x, dims, m_w, mu, seconds, min_steps=3, max_steps=10 ** 9, store=True):
+    """Run outer two-sided Lanczos steps of the oracle for about `seconds`; return
+    (seconds per step, the Outer object, steps)."""
     from oracle import dirac, krylov
 
-    fA = lambda v: dirac.A_apply(U, v, DIMS, M_W, MU)
-    fAH = lambda v: dirac.AH_apply(U, v, DIMS, M_W, MU)
-    out = krylov.Outer(fA, fAH, x, False)
+    out = krylov.Outer(lambda v: dirac.A_apply(U, v, dims, m_w, mu), lambda v: dirac.AH_apply(U, v, dims, m_w, mu),
+                       x, mu == 0.0, store=store)
     t0 = time.perf_counter()
     steps = 0
-    while steps < 3 or (time.perf_counter() - t0 < seconds_target * 0.8 and steps < k_used):
+    while steps < min_steps or (time.perf_counter() - t0 < seconds and steps < max_steps):
         out.step()
         steps += 1
-    t_step = (time.perf_counter() - t0) / steps
-    # one inner level at the GPU's k on a tridiagonal of that size whose
-    # coefficients repeat the sampled ones (the cost depends only on k and l)
+    return (time.perf_counter() - t0) / steps, out, steps
+
+
+def _time_inner(out, steps, k_used, l_used, hermitian=False):
+    """One inner level at the apply's k on a tridiagonal whose coefficients repeat the
+    sampled ones (its cost depends only on k and l); seconds."""
+    from oracle import krylov
+
     reps = int(np.ceil(k_used / steps))
     a = np.tile(np.asarray(out.alpha, dtype=complex), reps)[:k_used]
     b = np.tile(np.asarray(out.beta[1:steps + 1], dtype=complex), reps)[:k_used + 1]
     g = np.tile(np.asarray(out.gamma[1:steps + 1], dtype=complex), reps)[:k_used + 1]
-    Hbig = krylov.tridiag(a, np.concatenate([[0], b]), np.concatenate([[0], g]))
+    H = krylov.tridiag(a, np.concatenate([[0], b]), np.concatenate([[0], g]))
     t1 = time.perf_counter()
-    krylov.nested_sign_e1(Hbig, min(l_used, k_used), False)
-    t_inner = time.perf_counter() - t1
-    k_inner = k_used
+    krylov.nested_sign_e1(H, min(l_used, k_used), hermitian)
+    return time.perf_counter() - t1
+
+
+_WORKER_INPUTS = {}
+
+
+def _c3_worker(task):
+    """Pool worker (spawned process, one BLAS thread): a bounded sample of the headline
+    workload on one point source. Returns (seconds per outer step, seconds per inner level)."""
+    src, seconds, k_used, l_used = task
+    if "c3" not in _WORKER_INPUTS:
+        _WORKER_INPUTS["c3"] = make_inputs()
+    U, X = _WORKER_INPUTS["c3"]
+    t_step, out, steps = _time_outer(U, X[src % NRHS], DIMS, M_W, MU, seconds)
+    return t_step, _time_inner(out, steps, k_used, l_used)
+
+
+def c3_rate(t_step, t_inner, k_used, n_checks):
+    return 1.0 / (k_used * t_step + n_checks * t_inner)
+
+
+class OraclePool:
+    """The oracle on every host core this process may use: one spawned process per core,
+    each running the bounded sample on its own point source concurrently."""
+
+    def __init__(self):
+        import multiprocessing as mp
+
+        self.cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+
+    def c3(self, seconds, k_used, l_used, n_checks):
+        """applies/s of all cores together (each core its own source) and the samples."""
+        res = self.pool.map(_c3_worker, [(i, seconds, k_used, l_used) for i in range(self.cores)], chunksize=1)
+        return sum(c3_rate(ts, ti, k_used, n_checks) for ts, ti in res), res
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(pool, U, X, k_used, l_used, seconds, c5=None):
+    """The oracle (numpy FP64, as it stands) on the host cores, on bounded samples:
+    - C3 (the headline workload, one point source): outer two-sided steps for ~`seconds`
+      plus one inner level at the GPU's k, extrapolated to k_used steps and the checks of
+      the benchmark's schedule; on one core, and on every core (one source per core);
+    - C2 (8^4, mu = 0.3, tol 1e-10, k <= 800, l = 100): one whole apply, not extrapolated;
+    - C5 (24^3 x 48, mu = 0.1, two-pass): two outer steps, extrapolated to the GPU's k,
+      both passes and its checks.
+    Returns the baseline object (value: C3 applies/s on every core)."""
+    import ovinputs as oi
+    from oracle import dirac, krylov
+
     n_checks = max(1, (k_used - CHECK_FIRST) // CHECK_EVERY + 1)
-    t_apply = k_used * t_step + n_checks * t_inner
-    desc = (f"oracle (numpy FP64) on 1 RHS: {steps} two-sided Lanczos steps timed "
-            f"({t_step:.3f} s/step) and one inner level (l={min(l_used, k_inner)}) at k={k_inner}; "
-            f"extrapolated to k={k_used} steps + {n_checks} checks")
-    return 1.0 / t_apply, desc, steps * t_step + (time.perf_counter() - t1)
+    t0 = time.perf_counter()
+    ts1, out, steps = _time_outer(U, X[0], DIMS, M_W, MU, seconds * 0.8)
+    ti1 = _time_inner(out, steps, k_used, l_used)
+    one = c3_rate(ts1, ti1, k_used, n_checks)
+    del out
+    allc, res = pool.c3(seconds * 0.8, k_used, l_used, n_checks)
+    # C2 whole
+    d2 = (8, 8, 8, 8)
+    U2 = oi.gauge_field(d2, "near_unit", 0, eps=0.4)
+    x2 = oi.gaussian_source(d2, 1)
+    t2 = time.perf_counter()
+    _, i2 = krylov.sign_apply(lambda v: dirac.A_apply(U2, v, d2, -1.5, 0.3), lambda v: dirac.AH_apply(U2, v, d2, -1.5, 0.3),
+                              x2, False, 800, 100, 1e-10)
+    c2 = {"s_per_apply": time.perf_counter() - t2, "k": int(i2["k"]), "status": int(i2["status"]), "cores": 1,
+          "sample": "one whole apply (Gaussian source, checks every 10 steps), not extrapolated"}
+    out = {"value": allc, "unit": "applies/s", "cores": pool.cores, "kind": "oracle",
+           "sample": (f"C3: {steps} outer two-sided steps of the oracle (numpy FP64) on one point source per core "
+                      f"plus one inner level (l={l_used}) at k={k_used}, extrapolated to k={k_used} steps and "
+                      f"{n_checks} checks; the GPU run's k"),
+           "one_core": {"value": one, "s_per_step": ts1, "s_inner": ti1},
+           "all_cores": {"value": allc, "cores": pool.cores, "s_per_step": [r[0] for r in res],
+                         "s_inner": [r[1] for r in res]},
+           "c2_8x8x8x8_whole": c2}
+    if c5 is not None:
+        U5, x5, d5, k5, l5, checks5 = c5
+        ts5, out5, st5 = _time_outer(U5, x5, d5, -1.6, 0.1, 0.0, min_steps=2, max_steps=2, store=False)
+        ti5 = _time_inner(out5, st5, k5, l5)
+        out["c5_24x24x24x48_one_rhs"] = {
+            "s_per_apply": 2 * k5 * ts5 + checks5 * ti5, "s_per_step": ts5, "s_inner": ti5, "cores": 1,
+            "sample": f"2 outer steps timed, extrapolated to the GPU's k={k5} in both passes and {checks5} checks"}
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
+def alg_bytes_site(unit, N, p, p_link):
+    """Algorithmic bytes per lattice site of the units of work the measurement counts
+    (N right-hand sides sharing the links; p bytes per real of the vectors, p_link of the
+    links; 18 reals a link, 4 links a site, 24 reals a spinor):
+      stencil2: the fused +-mu stencil of two-sided Lanczos (A v and A^dag w): read v, w
+                and the links once, write A v and A^dag w: N*96p + 72p_link;
+      update2:  the vector pass the two-kernel design adds to a two-sided step (read p, r,
+                v_j, w_j, write the next v~, w~): N*144p;
+      step2:    the whole two-sided step, algorithmic (read v_j, v_{j-1}, w_j, w_{j-1} and the
+                links, write v_{j+1}, w_{j+1}): N*144p + 72p_link."""
+    return {"stencil2": N * 96 * p + 72 * p_link, "update2": N * 144 * p,
+            "step2": N * 144 * p + 72 * p_link}[unit]
+
+
+def oracle_sample_errors(y):
+    """Errors of the rows y[r] against the stored oracle values of source r (sampled
+    entries relative to their norm); None without the fixture."""
+    g = golden()
+    if g is None:
+        return None
+    idx = np.array([12 * s + c for s in g["sites"] for c in range(12)])
+    out = {}
+    for r, s in g["sources"].items():
+        ys = np.array([complex(*z) for z in s["y"]])
+        out[r] = float(np.linalg.norm(y[int(r)][idx] - ys) / np.linalg.norm(ys))
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
     import paper_0910_2918_gb300 as ov
 
+    # the oracle pool is spawned before any GPU work (rank 0, N = 1 only)
+    pool = OraclePool() if (rank == 0 and world == 1 and not args.no_cpu) else None
     torch.cuda.set_device(local_rank)
     dist = None
     if world > 1:
@@ -247,10 +381,10 @@ def run_ours(args, rank, world, local_rank):
     U, X = make_inputs()
     n = X.shape[1]
     stream = torch.cuda.Stream()
-    # checks: the learned first check, then every CHECK_EVERY steps (fixed schedule)
-    hkw = dict(check_interval=CHECK_EVERY, first_check=CHECK_FIRST, check_schedule=0, timing=1)
-    opts = ov.make_opts(relax=RELAX, **hkw)
-    op = ov.Overlap(DIMS, U, M_W, MU, PREC, opts=opts, stream=stream.cuda_stream)
+    # checks: the learned first check, then every CHECK_EVERY steps (fixed schedule); outer
+    # steps between checks replay CUDA graphs (timing off)
+    hkw = dict(check_interval=CHECK_EVERY, first_check=CHECK_FIRST, check_schedule=0)
+    op = ov.Overlap(DIMS, U, M_W, MU, PREC, opts=ov.make_opts(relax=RELAX, **hkw), stream=stream.cuda_stream)
     # learned sizing: the committed network predicts the first check and l after 16 steps
     sized = not args.no_sizer
     if sized:
@@ -269,7 +403,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         rc, info = op.sign_apply(xd, yd, TOL_STOP, K_MAX, L_INNER)
     torch.cuda.synchronize()
-    # timed region: device-resident inputs
+    # timed region: device-resident inputs, graphs replayed, no per-kernel events
     op.reset_stats()
     barrier()
     torch.cuda.synchronize()
@@ -284,6 +418,13 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms = e0.elapsed_time(e1)
     st = op.stats()
+    # per-kernel durations: one more apply of the same form with CUDA events around every
+    # launch on the handle's stream (plain launches), outside the timed region
+    op.set_opts(relax=RELAX, timing=1, **hkw)
+    op.reset_stats()
+    op.sign_apply(xd, yd, TOL_STOP, K_MAX, L_INNER)
+    stk = op.stats()
+    op.set_opts(relax=RELAX, **hkw)
     # end to end: host buffers, copies inside the call
     barrier()
     torch.cuda.synchronize()
@@ -297,7 +438,6 @@ def run_ours(args, rank, world, local_rank):
     ys = torch.zeros_like(xd)
     op.set_opts(**hkw)
     op.sign_apply(xd, ys, TOL_STOP, K_MAX, L_INNER)
-    op.reset_stats()
     barrier()
     torch.cuda.synchronize()
     e0.record(stream)
@@ -307,11 +447,16 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     ms_strict = e0.elapsed_time(e1)
-    st_strict = op.stats()
+    op.set_opts(timing=1, **hkw)
+    op.reset_stats()
+    op.sign_apply(xd, ys, TOL_STOP, K_MAX, L_INNER)
+    stk_strict = op.stats()
     op.set_opts(relax=RELAX, **hkw)
     ms_max, e2e_ms, ms_strict_max = rank_max(dist, [ms, t_e2e * 1e3, ms_strict], "cuda")
-    # the float (mixed-precision) stencil on the same workload: HBM fraction of its fused
-    # two-sided step (k fixed, outside the timed region)
+    V = int(np.prod(DIMS))
+    hbm_pk = (peaks() or {}).get("hbm_gbs")
+    # the float (mixed-precision) step kernel on the same workload (k fixed, outside the
+    # timed region): its HBM fraction by the fused-stencil unit at 4 bytes a real
     fp32_stencil = None
     if rank == 0 and not args.no_fp32:
         with ov.Overlap(DIMS, U, M_W, MU, "fp32", opts=ov.make_opts(k_fixed=60, timing=1),
@@ -321,19 +466,22 @@ def run_ours(args, rank, world, local_rank):
             op32.reset_stats()
             op32.sign_apply(xd, y32, TOL, K_MAX, 8)
             s32 = op32.stats()
-        V = int(np.prod(DIMS))
-        b32 = V * (NRHS * 8 * 12 * 8 + 4 * 9 * 8)
+        b32 = V * alg_bytes_site("stencil2", NRHS, 4, 4)
         t32 = s32["stencil_ms"] / max(s32["stencil_launches"], 1)
+        u32 = s32["update_ms"] / max(s32["update_launches"], 1)
         fp32_stencil = {"kernel": "k_step<PrecF32, two-sided>", "alg_bytes_per_launch": b32, "avg_launch_ms": t32,
                         "achieved_gbs": b32 / (t32 * 1e-3) / 1e9,
-                        "frac_of_measured_hbm": b32 / (t32 * 1e-3) / 1e9 / (peaks() or {}).get("hbm_gbs", 6800.0),
-                        "block_size": s32["block_size"]}
+                        "frac": b32 / (t32 * 1e-3) / 1e9 / (hbm_pk or 6800.0),
+                        "update_avg_launch_ms": u32,
+                        "update_frac": V * alg_bytes_site("update2", NRHS, 4, 4) / (u32 * 1e-3) / 1e9 / (hbm_pk or 6800.0),
+                        "block_size": s32["block_size"],
+                        "unit": "fused +-mu stencil, N*96p + 72p bytes a site, p = 4"}
     # the plain FP64 nested method (FP64 vectors, one RHS at a time, checks every 10 steps,
     # no sizing) on a sample of the same RHS: the speedup of the fast form at equal accuracy
     plain = None
     if rank == 0 and not args.no_plain:
         sel = [0, 7]
-        t_plain, err_plain = 0.0, 0.0
+        t_plain = 0.0
         with ov.Overlap(DIMS, U, M_W, MU, "fp64", opts=ov.make_opts(check_interval=10,
                                                                     inner_arith=ov.binding.OV_INNER_FP64),
                         stream=stream.cuda_stream) as opp:
@@ -351,9 +499,11 @@ def run_ours(args, rank, world, local_rank):
                  "form": "FP64 vectors and inner level, one RHS per call, checks every 10 steps, l=%d, "
                          "no sizing" % L_INNER}
     # accuracy of every apply against the double-precision path (outside the timed region):
-    # the same 12 sources with FP64 vectors and links, stopped at 1e-10
+    # the same 12 sources with FP64 vectors and links, stopped at 1e-10; that path and the
+    # headline itself are also compared with the oracle's stored answers for two sources
     errs = None
     mixed = None
+    vs_oracle = None
     if not args.no_validate:
         with ov.Overlap(DIMS, U, M_W, MU, "fp64", opts=ov.make_opts(check_interval=CHECK_EVERY,
                                                                     first_check=CHECK_FIRST, check_schedule=1,
@@ -365,13 +515,16 @@ def run_ours(args, rank, world, local_rank):
             errs_strict = [float(torch.linalg.norm(ys[r] - yr[r]) / torch.linalg.norm(yr[r])) for r in range(NRHS)]
             errs_e2e = [float(torch.linalg.norm(yh[r].cuda() - yr[r]) / torch.linalg.norm(yr[r]))
                         for r in range(NRHS)]
+        vs_oracle = {"headline": oracle_sample_errors(yd.cpu().numpy()),
+                     "fp64_path": oracle_sample_errors(yr.cpu().numpy()),
+                     "what": "relative error on the stored oracle samples of y (tests/golden, written by the oracle)"}
         good = args.steps * sum(1 for e in errs if e <= TOL)
         good_e2e = args.steps * sum(1 for e in errs_e2e if e <= TOL)
         good_strict = args.steps * sum(1 for e in errs_strict if e <= TOL)
         # the mixed-precision path (float vectors and links, coefficients in double) on the
         # same sources at its own bar, 1e-6, against the same FP64 reference
         if rank == 0 and not args.no_fp32:
-            opts32 = ov.make_opts(check_interval=CHECK_EVERY, first_check=CHECK_FIRST, timing=1)
+            opts32 = ov.make_opts(check_interval=CHECK_EVERY, first_check=CHECK_FIRST)
             with ov.Overlap(DIMS, U, M_W, MU, "fp32", opts=opts32, stream=stream.cuda_stream) as op32:
                 y32 = torch.zeros_like(xd)
                 op32.sign_apply(xd, y32, MIXED_STOP, K_MAX, L_INNER)
@@ -387,6 +540,7 @@ def run_ours(args, rank, world, local_rank):
             ok32 = sum(1 for e in e32 if e <= TOL_MIXED) / NRHS
             mixed = {"applies_per_s": NRHS * MIXED_REPS / (t32 * 1e-3) * ok32, "tol": TOL_MIXED,
                      "stop_tol": MIXED_STOP, "applies_within_tol": ok32, "rel_err_vs_fp64_path_max": max(e32),
+                     "rel_err_vs_oracle_sampled": oracle_sample_errors(y32.cpu().numpy()),
                      "k_used": max(i["k"] for i in info32), "l_used": max(i["l"] for i in info32),
                      "form": "float vectors and links, double coefficients, checks at %d then every %d, l=%d"
                              % (CHECK_FIRST, CHECK_EVERY, L_INNER)}
@@ -403,47 +557,42 @@ def run_ours(args, rank, world, local_rank):
         return None
     k_used = max(i["k"] for i in info)
     l_used = max(i["l"] for i in info)
-    extra = extra_configs(ov, torch) if not args.no_extra else None
-    pk = peaks() or {}
-    hbm = pk.get("hbm_gbs")
+    extra, c5_in = extra_configs(ov, torch) if not args.no_extra else (None, None)
+    hbm = hbm_pk
     peak_src = "of measured" if hbm else "of fallback"
     hbm = hbm or 6800.0
-    # the two step kernels of the timed region (fused two-sided stencil + recurrence, strict
-    # and relaxed); algorithmic bytes per launch: 8 spinor passes of 16-byte complex per site
-    # and RHS plus the links once (float pairs strict, high words relaxed)
-    V = int(np.prod(DIMS))
+    # the kernels of the headline path with their shares of one apply (per-kernel events of
+    # the untimed pass), algorithmic bytes per launch by the units of alg_bytes_site
     clk_summary = clk.summary()
+    n_rel, ms_rel = stk["relaxed_steps"], stk["relaxed_ms"]
+    n_str, ms_str = stk["stencil_launches"] - n_rel, stk["stencil_ms"] - ms_rel
     kernels = []
-    n_rel, ms_rel = st["relaxed_steps"], st["relaxed_ms"]
-    n_str, ms_str = st["stencil_launches"] - n_rel, st["stencil_ms"] - ms_rel
-    for name, n_k, ms_k, lb, prof in (
+    for name, n_k, ms_k, unit, p_link, prof in (
             ("k_step<PrecDF64, two-sided> (fused A, A^dag stencil + recurrence, double-float)", n_str, ms_str,
-             4 * 9 * 16, PROFILE),
-            ("k_step<PrecDF64R, two-sided> (float hopping, double-float recurrence)", n_rel, ms_rel, 4 * 9 * 8,
-             PROFILE_RELAXED)):
+             "stencil2", 8, PROFILE),
+            ("k_step<PrecDF64R, two-sided> (float hopping, double-float recurrence)", n_rel, ms_rel, "stencil2", 4,
+             PROFILE_RELAXED),
+            ("k_update<PrecDF64, two-sided> (vector update, double-float)", stk["update_launches"], stk["update_ms"],
+             "update2", 8, None)):
         if n_k <= 0:
             continue
-        ab = V * (NRHS * 8 * 12 * 16 + lb)
+        ab = V * alg_bytes_site(unit, NRHS, 8, p_link)
         avg = ms_k / n_k
-        # instruction issue: 152 SMs x 4 schedulers x 1 warp instruction per clock
-        wi = profile_inst(prof)
-        sm_hz = (clk_summary.get("sm_mhz") or 2070.0) * 1e6
-        issue = None if wi is None else {
-            "warp_inst_per_launch": wi, "achieved_ginst_s": wi / (avg * 1e-3) / 1e9,
-            "peak_ginst_s": 152 * 4 * sm_hz / 1e9, "frac": wi / (avg * 1e-3) / (152 * 4 * sm_hz),
-            "source": "ncu smsp__inst_executed.sum of the committed profile / live launch time"}
-        kernels.append({"kernel": name, "launches_per_step": n_k / args.steps, "total_ms_per_step": ms_k / args.steps,
-                        "alg_bytes_per_launch": ab, "avg_launch_ms": avg, "achieved_gbs": ab / (avg * 1e-3) / 1e9,
-                        "traffic": profile_traffic(prof), "issue": issue})
-    dom = max(kernels, key=lambda q: q["total_ms_per_step"])
-    alg_bytes, st_ms, achieved, traffic = dom["alg_bytes_per_launch"], dom["avg_launch_ms"], dom["achieved_gbs"], \
-        dom["traffic"]
+        traffic = profile_traffic(prof) if prof else None
+        kernels.append({"kernel": name, "launches_per_apply": n_k, "ms_per_apply": ms_k,
+                        "share_of_apply": ms_k / max(stk["total_ms"], 1e-9), "alg_bytes_per_launch": ab,
+                        "unit": unit, "avg_launch_ms": avg, "achieved_gbs": ab / (avg * 1e-3) / 1e9,
+                        "frac": ab / (avg * 1e-3) / 1e9 / hbm, "traffic": traffic,
+                        "traffic_over_alg": traffic / ab if traffic else None})
+    dom = max(kernels, key=lambda q: q["ms_per_apply"])
+    n_steps = stk["stencil_launches"]
+    step2 = V * alg_bytes_site("step2", NRHS, 8, 8)
+    t_step2 = (stk["stencil_ms"] + stk["update_ms"]) / max(n_steps, 1)
     good_frac = good_all / (world * NRHS * args.steps)
     cpu = None
-    if not args.no_cpu:
-        v, desc, spent = oracle_sample(U, X[0], k_used, l_used, args.cpu_seconds)
-        cpu = {"value": v, "unit": "applies/s", "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": round(spent, 1)}
+    if pool is not None:
+        cpu = cpu_baseline(pool, U, X, k_used, l_used, args.cpu_seconds, c5=c5_in)
+        pool.close()
     line = {
         "metric": METRIC,
         "value": whole_job(good_all, ms_max),
@@ -460,24 +609,32 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": workload_desc(), "global_batch": NRHS * world, "parallelism": f"replicas{world}",
                    "learned_sizing": sized,
                    "l2": "working set per step >> L2 (12 x k x 12.6 MB stored basis)", "k_used": k_used,
-                   "l_used": l_used, "relax": RELAX, "relaxed_steps_per_apply": n_rel / args.steps,
+                   "l_used": l_used, "relax": RELAX, "relaxed_steps_per_apply": st["relaxed_steps"] / args.steps,
                    "stop_tol": TOL_STOP, "applies_within_tol": good_frac,
-                   "rel_err_vs_fp64_path_max": max(errs) if errs else None},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": traffic, "kernel": dom["kernel"],
-                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": st_ms, "peak_source": peak_src,
-                     "block_size": st["block_size"]},
-        "step_kernels": [dict(q, frac=q["achieved_gbs"] / hbm) for q in kernels],
+                   "rel_err_vs_fp64_path_max": max(errs) if errs else None,
+                   "rel_err_vs_oracle_sampled": vs_oracle,
+                   "timed_region": "graphs of 8 outer steps replayed between checks, no per-kernel events"},
+        "roofline": {"bound": "hbm", "achieved": dom["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                     "frac": dom["achieved_gbs"] / hbm, "traffic": dom["traffic"], "kernel": dom["kernel"],
+                     "alg_bytes_per_launch": dom["alg_bytes_per_launch"], "unit_of_work": dom["unit"],
+                     "traffic_over_alg": dom["traffic_over_alg"], "avg_launch_ms": dom["avg_launch_ms"],
+                     "peak_source": peak_src, "block_size": stk["block_size"],
+                     "timing": "CUDA events around every launch on the handle's stream, one apply after the "
+                               "timed region (plain launches)"},
+        "kernels": kernels,
+        "step_2sl": {"alg_bytes_per_step": step2, "unit": "step2", "avg_step_ms": t_step2,
+                     "achieved_gbs": step2 / (t_step2 * 1e-3) / 1e9, "frac": step2 / (t_step2 * 1e-3) / 1e9 / hbm,
+                     "what": "whole two-sided step (stencil kernel + update kernel) against the algorithmic "
+                             "bytes of one step"},
         "strict_df64": {"applies_per_s": whole_job(good_strict_all, ms_strict_max),
                         "ms_per_step": ms_strict_max / args.steps, "k_used": max(i["k"] for i in info_s),
                         "applies_within_tol": good_strict_all / (world * NRHS * args.steps),
                         "rel_err_vs_fp64_path_max": max(errs_strict) if errs_strict else None,
-                        "stencil_ms_per_launch": st_strict["stencil_ms"] / max(st_strict["stencil_launches"], 1),
+                        "stencil_ms_per_launch": stk_strict["stencil_ms"] / max(stk_strict["stencil_launches"], 1),
                         "form": "every hopping sum in float pairs (no relaxed steps)"},
-        "phase_ms_per_step": {"stencil": st["stencil_ms"] / args.steps, "stencil_relaxed": ms_rel / args.steps,
-                              "update": st["update_ms"] / args.steps,
-                              "inner": st["inner_ms"] / args.steps, "recombine": st["recombine_ms"] / args.steps,
-                              "checks": st["checks"] / args.steps},
+        "phase_ms_per_apply": {"stencil": stk["stencil_ms"], "stencil_relaxed": ms_rel, "update": stk["update_ms"],
+                               "inner": stk["inner_ms"], "recombine": stk["recombine_ms"], "total": stk["total_ms"],
+                               "checks": stk["checks"]},
         "other_workloads": extra,
         "stencil_fp32": fp32_stencil,
         "mixed_fp32": mixed,
@@ -517,7 +674,8 @@ def extra_configs(ov, torch):
     mws, mus = [p["m_w"] for p in probs], [p["mu"] for p in probs]
     res = {}
     theta = sizer.load(sizer.DEFAULT_PARAMS)
-    for form, prec, tol, ob in (("fp32", "fp32", MIXED_STOP, dict(check_interval=CHECK_EVERY, first_check=CHECK_FIRST)),
+    for form, prec, tol, ob in (("fp32", "fp32", BATCH_FP32_STOP, dict(check_interval=CHECK_EVERY,
+                                                                        first_check=CHECK_FIRST)),
                                 ("fp64", "fp64", 1e-10, dict(check_interval=10)),
                                 ("df64", "df64", TOL_STOP, dict(check_interval=CHECK_EVERY, first_check=CHECK_FIRST,
                                                                 relax=RELAX))):
@@ -542,14 +700,17 @@ def extra_configs(ov, torch):
         out["batch48_" + form] = {
             "problems_per_s": 48 / secs, "ms": secs * 1e3, "converged": len(ok), "bar": bar,
             "rel_err_vs_fp64_path_max": max(errs) if errs else None, "within_bar": sum(e <= bar for e in errs),
+            "stop_tol": BATCH_FP32_STOP if form == "fp32" else TOL_STOP,
             "outer_steps": st["outer_steps"], "relaxed_steps": st["relaxed_steps"],
             "graph_launches": st["graph_launches"], "block_size": st["block_size"],
             "form": ("float vectors and links" if form == "fp32" else
                      "double-float, learned sizing, float hopping from %.1f x k* on" % RELAX)
             + "; one handle, one launch per outer step for all 48 lattices, CUDA graphs of 8 steps"}
     dims = (24, 24, 24, 48)
-    U = torch.from_numpy(oi.gauge_field(dims, "near_unit", 0, eps=0.3)).cuda()
-    x = torch.from_numpy(oi.gaussian_source(dims, 1).reshape(1, -1)).cuda()
+    U5 = oi.gauge_field(dims, "near_unit", 0, eps=0.3)
+    x5 = oi.gaussian_source(dims, 1)
+    U = torch.from_numpy(U5).cuda()
+    x = torch.from_numpy(x5.reshape(1, -1)).cuda()
     yr = torch.zeros_like(x)
     with ov.Overlap(dims, U, -1.6, 0.1, "fp64", opts=ov.make_opts(check_interval=25, first_check=100,
                     recombination=1, inner_arith=ov.binding.OV_INNER_FP64)) as op:
@@ -573,7 +734,67 @@ def extra_configs(ov, torch):
                     "checks": st["checks"], "regen_steps": st["regen_steps"], "relaxed_steps": st["relaxed_steps"],
                     "rel_err_vs_fp64_path": float(torch.linalg.norm(y - yr) / torch.linalg.norm(yr))}
     out["c5_24x24x24x48_two_pass"] = c5
-    return out
+    # the oracle's C5 sample extrapolates to the sized run's k, l and checks
+    c5_in = (U5, x5, dims, c5["sized_relaxed"]["k"], c5["sized_relaxed"]["l"], c5["sized_relaxed"]["checks"])
+    return out, c5_in
+
+
+SWEEP_VOLUMES = [(4, 4, 4, 4), (6, 6, 6, 6), (8, 8, 8, 8), (10, 10, 10, 10), (12, 12, 12, 12), (16, 16, 16, 16),
+                 (20, 20, 20, 20), (24, 24, 24, 48)]
+
+
+def fit_exponent(vols, times):
+    """Least-squares slope of log t against log V."""
+    lv, lt = np.log(np.asarray(vols, dtype=float)), np.log(np.asarray(times, dtype=float))
+    return float(np.polyfit(lv, lt, 1)[0])
+
+
+def run_volume_sweep(args):
+    """Time per apply against lattice volume (Sec. 4, the volume-scaling figure): near-unit
+    links exp(i 0.3 H) (seed 0), m_w = -1.6, one Gaussian source (seed 1), mu = 0 and 0.3,
+    accuracy 1e-8 (stop at 5e-9 on the estimate, a check every 10 steps, l = 120),
+    double-float vectors and links, stored basis (single pass) and regenerated
+    basis (double pass); exponent alpha of t ~ V^alpha by a least-squares fit, over all
+    volumes and over V >= 8^4 (below that the GPU is far from full)."""
+    import torch
+
+    import ovinputs as oi
+    import paper_0910_2918_gb300 as ov
+
+    rows = []
+    for dims in SWEEP_VOLUMES:
+        V = int(np.prod(dims))
+        U = torch.from_numpy(oi.gauge_field(dims, "near_unit", 0, eps=0.3)).cuda()
+        x = torch.from_numpy(oi.gaussian_source(dims, 1).reshape(1, -1)).cuda()
+        for mu in (0.0, 0.3):
+            for recomb, name in ((0, "single"), (1, "double")):
+                y = torch.zeros_like(x)
+                with ov.Overlap(dims, U, -1.6, mu, "df64", opts=ov.make_opts(check_interval=10,
+                                                                             recombination=recomb)) as op:
+                    op.sign_apply(x, y, TOL_STOP, K_MAX, L_MAX)
+                    torch.cuda.synchronize()
+                    reps = 3
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(reps):
+                        rc, info = op.sign_apply(x, y, TOL_STOP, K_MAX, L_MAX)
+                    e1.record()
+                    torch.cuda.synchronize()
+                rows.append({"dims": list(dims), "V": V, "mu": mu, "pass": name, "k": info[0]["k"], "l": info[0]["l"],
+                             "status": info[0]["status"], "ms": e0.elapsed_time(e1) / reps})
+        del U, x
+        torch.cuda.empty_cache()
+    fits = {}
+    for mu in (0.0, 0.3):
+        for name in ("single", "double"):
+            sel = [r for r in rows if r["mu"] == mu and r["pass"] == name and r["status"] == 0]
+            big = [r for r in sel if r["V"] >= 8 ** 4]
+            fits[f"mu{mu}_{name}"] = {
+                "alpha_all": fit_exponent([r["V"] for r in sel], [r["ms"] for r in sel]) if len(sel) > 1 else None,
+                "alpha_V_ge_8^4": fit_exponent([r["V"] for r in big], [r["ms"] for r in big]) if len(big) > 1 else None}
+    print(json.dumps({"volume_sweep": rows, "fits": fits,
+                      "paper": "t ~ V^1.2 (mu = 0) and V^1.4 (mu = 0.3) on the paper's CPU with deflation"}),
+          flush=True)
 
 
 def run_profile(args):
@@ -595,18 +816,30 @@ def run_profile(args):
 
 
 def run_reference(args, rank, world):
-    """The oracle as it stands, on the host cores, on the same workload and metric."""
+    """The oracle as it stands, on every host core this process may use (one point source
+    per core, concurrently), on the headline workload and metric. Each step is a bounded
+    sample: outer two-sided steps for a few seconds and one inner level at the oracle's own
+    stopping step, extrapolated to that step count and the benchmark's checks."""
     if rank != 0:
         return None
-    U, X = make_inputs()
-    k_assumed, l_used = 333, L_INNER  # where the stopping rule stops on this workload (measured on the GPU)
+    k_stop, k_src = oracle_k_stop()
+    l_used = L_INNER
+    n_checks = max(1, (k_stop - CHECK_FIRST) // CHECK_EVERY + 1)
+    per_step = max(1.5, min(args.cpu_seconds / 3, 120.0 / max(1, args.steps + args.warmup)))
+    pool = OraclePool()
     vals = []
-    desc = None
-    for i in range(args.warmup + args.steps):
-        v, desc, _ = oracle_sample(U, X[i % NRHS], k_assumed, l_used, seconds_target=args.cpu_seconds / 3)
-        if i >= args.warmup:
-            vals.append(v)
+    res = None
+    try:
+        for i in range(args.warmup + args.steps):
+            v, res = pool.c3(per_step, k_stop, l_used, n_checks)
+            if i >= args.warmup:
+                vals.append(v)
+    finally:
+        pool.close()
     value = float(np.mean(vals))
+    desc = (f"C3: outer two-sided steps of the oracle (numpy FP64, one BLAS thread) for ~{per_step:.1f} s on one "
+            f"point source per core ({pool.cores} cores concurrently) plus one inner level (l={l_used}) at "
+            f"k={k_stop}, extrapolated to k={k_stop} steps and {n_checks} checks; k from the {k_src}")
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -621,8 +854,9 @@ def run_reference(args, rank, world):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_desc(), "k_assumed": k_assumed},
-        "cpu_baseline": {"value": value, "unit": "applies/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "config": {"workload": workload_desc(), "k_oracle_stop": k_stop, "k_source": k_src},
+        "cpu_baseline": {"value": value, "unit": "applies/s", "cores": pool.cores, "kind": "oracle", "sample": desc,
+                         "s_per_step_last": [r[0] for r in res] if res else None},
         "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -646,6 +880,9 @@ def main():
                     help="arithmetic of the profiling run")
     ap.add_argument("--profile-relax", type=float, default=0.0,
                     help="with --profile-steps: float hopping from step relax x steps on")
+    ap.add_argument("--volume-sweep", action="store_true",
+                    help="time per apply against lattice volume (4^4 .. 24^3x48), mu = 0 and 0.3, single and "
+                         "double pass, with the fitted exponent of t ~ V^alpha; prints one JSON line")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling run: one batched apply of the bench workload with exactly this many "
                          "outer steps (no timing, baseline or validation); for ncu captures")
@@ -655,6 +892,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.profile_steps > 0:
         run_profile(args)
+    elif args.volume_sweep:
+        run_volume_sweep(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

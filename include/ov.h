@@ -40,6 +40,12 @@
  * best estimate and info->err_est is set) or a negative error; ov_strerror() names it.
  * There is no CPU fallback: without a usable CUDA device every call fails with
  * OV_ERR_CUDA.
+ *
+ * Environment, read by ov_create: OV_TRACE (set: one JSON line per stopping check on
+ * stderr); OV_BASIS_CAP_BYTES (a byte count: the stored Krylov basis of the handle may
+ * not grow beyond it, as if device memory ran out there; with OV_RECOMB_AUTO the run then
+ * continues in the double pass; meant for testing that fall-back). Phases of an apply
+ * (outer steps, stopping checks, recombination) are marked as NVTX ranges.
  */
 #ifndef OV_H
 #define OV_H
@@ -127,6 +133,10 @@ typedef struct {
                            are those of the serial order (not used where the previous check's
                            largest outer estimate was within 8 tol, where a stop is likely);
                            0: checks block the outer steps [1] */
+  int nested;           /* 1: the nested method (Sec. 3); 0: the non-nested method (Sec. 2): every
+                           stopping check takes c = sgn(H_k) e_1 by Roberts-Higham on the full
+                           k x k Ritz matrix (FP64 Gauss-Jordan inversions over global memory,
+                           k <= 1024; the inner estimate is 0), for comparing the two [1] */
 } ov_opts;
 
 #define OV_INNER_DF64 0
@@ -228,9 +238,12 @@ int ov_inner_sign(ov_handle* h, int count, int ld, const int* k, const void* alp
                   double* est_inner, int* rh_iters);
 
 /* Roberts-Higham alone (Sec. 2, Eq. (Roberts)): S = sgn(T) for `count` dense m x m
- * matrices (row-major complex doubles, HOST memory, m <= 120), written to S (host), with
- * the Gauss-Jordan inversions in the handle's opts.inner_arith.
- * Returns OV_ERR_RH_NOCONV if any matrix did not converge within opts.rh_maxit. */
+ * matrices (row-major complex doubles, HOST memory, m <= 1024), written to S (host). For
+ * m <= 120 one CTA inverts each matrix in shared memory, in the handle's opts.inner_arith;
+ * for larger m (the non-nested method's full Ritz matrices) a batched Gauss-Jordan
+ * elimination with partial pivoting runs over global memory in FP64, one launch per pivot
+ * column. Returns OV_ERR_RH_NOCONV if any matrix did not converge within opts.rh_maxit
+ * (or met an exactly singular pivot), OV_ERR_TOO_LARGE for m > 1024. */
 int ov_rh_sign(ov_handle* h, int count, int m, const void* T, void* S, int* iters);
 
 /* ---- learned sizing of the Krylov dimensions (not in the paper) ----
@@ -283,8 +296,9 @@ int ov_get_coefficients(const ov_handle* h, int rhs, int kcap, void* alpha, void
  * on it, so serialise them (one stream, or wait between calls). The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with the device
  * current; make that first call before any stream capture. Returns OV_ERR_RH_NOCONV if
- * a matrix did not converge within rh_maxit, and returns after `stream` (a cudaStream_t
- * or NULL) has finished the call's work. */
+ * a matrix did not converge within rh_maxit (or an inversion met an exactly singular
+ * pivot), and returns after `stream` (a cudaStream_t or NULL) has finished the call's
+ * work: the call blocks the host until then, to read the per-matrix flags. */
 int ov_rh_sign_noalloc(int count, int m, const void* T, void* S, int* iters, double rh_tol,
                        int rh_maxit, void* stream);
 

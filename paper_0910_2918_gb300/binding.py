@@ -48,7 +48,7 @@ class ov_opts(ctypes.Structure):
                 ("breakdown_tol", ctypes.c_double), ("inner_dl", ctypes.c_int), ("k_fixed", ctypes.c_int),
                 ("check_schedule", ctypes.c_int), ("block_size", ctypes.c_int), ("graph_steps", ctypes.c_int),
                 ("timing", ctypes.c_int), ("inner_arith", ctypes.c_int), ("relax", ctypes.c_double),
-                ("overlap_checks", ctypes.c_int)]
+                ("overlap_checks", ctypes.c_int), ("nested", ctypes.c_int)]
 
 
 class ov_stats(ctypes.Structure):
@@ -334,11 +334,22 @@ def ov_rh_sign_noalloc(T, S, rh_tol=1e-10, rh_maxit=100, stream=None):
         raise ValueError("T and S must be CUDA tensors")
     _check_c128(T, "T")
     _check_c128(S, "S")
+    # the kernel reads count * m * m entries of T and writes as many of S
+    if T.dim() != 3 or T.shape[1] != T.shape[2]:
+        raise ValueError(f"T must have shape (count, m, m), got {tuple(T.shape)}")
+    if tuple(S.shape) != tuple(T.shape):
+        raise ValueError(f"S must have T's shape {tuple(T.shape)}, got {tuple(S.shape)}")
+    if S.device != T.device:
+        raise ValueError("T and S must be on the same device")
+    import torch
+
     count, m = int(T.shape[0]), int(T.shape[1])
     its = np.zeros(count, dtype=np.int32)
-    rc = lib().ov_rh_sign_noalloc(count, m, tp, sp, its.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                                  float(rh_tol), int(rh_maxit),
-                                  ctypes.c_void_p(stream) if stream is not None else None)
+    with torch.cuda.device(T.device):
+        # default: torch's current stream on T's device, so work queued there on T comes first
+        st = stream if stream is not None else torch.cuda.current_stream(T.device).cuda_stream
+        rc = lib().ov_rh_sign_noalloc(count, m, tp, sp, its.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      float(rh_tol), int(rh_maxit), ctypes.c_void_p(st) if st else None)
     if rc < 0 and rc != OV_ERR_RH_NOCONV:
         raise OvError(rc, "ov_rh_sign_noalloc")
     return rc, its

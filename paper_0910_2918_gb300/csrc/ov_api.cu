@@ -28,9 +28,20 @@
 #include <map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ov_internal.h"
 
 using namespace ov;
+
+// NVTX range around a phase (outer steps, a check, recombination), for timeline tools;
+// costs a few nanoseconds when no tool is attached
+struct Phase {
+  explicit Phase(const char* name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+  Phase(const Phase&) = delete;
+  Phase& operator=(const Phase&) = delete;
+};
 
 namespace {
 
@@ -125,6 +136,8 @@ struct ov_handle {
   // the last apply (for ov_get_coefficients)
   int last_steps = 0, last_ld = 0, last_nrhs = 0;
   int trace = 0;  // OV_TRACE set in the environment: one JSON line per check on stderr
+  size_t basis_cap = 0;  // OV_BASIS_CAP_BYTES: bytes the stored basis may take (0: no cap)
+  Buf nn_scratch;        // the non-nested check's dense H_k, iterates and elimination buffers
   // event pairs recorded around timed launches: (class, start, stop)
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_class;
@@ -274,6 +287,7 @@ extern "C" void ov_default_opts(ov_opts* o) {
   o->inner_arith = OV_INNER_DF64;
   o->relax = 0.0;
   o->overlap_checks = 1;
+  o->nested = 1;
 }
 
 extern "C" const char* ov_strerror(int code) {
@@ -296,7 +310,8 @@ static int check_opts(const ov_opts& o) {
       o.check_schedule < 0 || o.check_schedule > 1 ||
       (o.block_size != 0 && o.block_size != 64 && o.block_size != 128 && o.block_size != 256) ||
       o.graph_steps < 0 || o.graph_steps > 256 || o.inner_arith < 0 || o.inner_arith > 1 ||
-      !(o.relax >= 0.0 && o.relax <= 1.0) || o.overlap_checks < 0 || o.overlap_checks > 1)
+      !(o.relax >= 0.0 && o.relax <= 1.0) || o.overlap_checks < 0 || o.overlap_checks > 1 || o.nested < 0 ||
+      o.nested > 1)
     return OV_ERR_ARG;
   return OV_OK;
 }
@@ -376,6 +391,7 @@ extern "C" int ov_create(ov_handle** hp, const ov_geom* geom, const void* links,
   h->antiperiodic = geom->t_antiperiodic ? 1 : 0;
   h->o = o;
   h->trace = getenv("OV_TRACE") != nullptr;
+  if (const char* cap = getenv("OV_BASIS_CAP_BYTES")) h->basis_cap = (size_t)strtoull(cap, nullptr, 10);
   const size_t canon = sizeof(double2) * 36 * (size_t)V;
   const double2* src = (const double2*)links;
   Buf tmp;
@@ -415,7 +431,7 @@ extern "C" void ov_destroy(ov_handle* h) {
                 &h->coef_kbreak, &h->partials, &h->counters, &h->scale, &h->scal, &h->iQ, &h->iT, &h->ileff, &h->iS, &h->is,
                 &h->irh_its, &h->irh_ok, &h->iperm, &h->ifail, &h->ck, &h->cl, &h->ckprev, &h->cc_cur, &h->cc_prev,
                 &h->cc_fin, &h->cacc_cur, &h->cacc_fin, &h->c_est_in, &h->c_est_out, &h->c_rhst, &h->c_rhit,
-                &h->vptr, &h->sizer_theta, &h->sizer_feat, &h->sizer_pred};
+                &h->vptr, &h->sizer_theta, &h->sizer_feat, &h->sizer_pred, &h->nn_scratch};
   for (Buf* b : all) release(*b);
   for (Buf& b : h->chunks) release(b);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -527,6 +543,9 @@ static int basis_slot(ov_handle* h, size_t pool_bytes, int slot, void** out) {
   }
   const int c = slot / kChunk;
   while ((int)h->chunks.size() <= c) {
+    // a cap on the stored basis set from the environment (OV_BASIS_CAP_BYTES) behaves like
+    // device memory running out at that point: how the fall-back to the double pass is tested
+    if (h->basis_cap > 0 && pool_bytes * kChunk * (h->chunks.size() + 1) > h->basis_cap) return OV_ERR_NOMEM;
     Buf b;
     cudaError_t e = grow(b, pool_bytes * kChunk);
     if (e != cudaSuccess) {
@@ -585,6 +604,7 @@ static int graph_for(ov_handle* h, const StepArgs& a, int prec, int mode, int U,
 // ---------------------------------------------------------------- sign apply
 static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,
                            ov_info* info, int add_x) {
+  const Phase ph_apply("ov_sign_apply");
   if (!h || !x || !y || nrhs < 1 || k_max < 1 || l < 1 || !(tol >= 0.0)) return OV_ERR_ARG;
   if (mem != OV_MEM_HOST && mem != OV_MEM_DEVICE) return OV_ERR_ARG;
   if (l > kMaxL) return OV_ERR_TOO_LARGE;
@@ -635,27 +655,35 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   CK(cudaMemsetAsync(h->vring.p, 0, 2 * vbn, st));
   CK(cudaMemsetAsync(h->wring.p, 0, 2 * vbn, st));
   // v_1 = w_1 = x / ||x||: x goes to tv (and tw), the norm into nv_1 / nw_1
-  CK(launch_pack(h->prec, bt, xd, h->tv.p, c, (double*)h->partials.p, (unsigned*)h->counters.p, 1, h->scal.p, st));
-  if (!herm) CK(cudaMemcpyAsync(h->tw.p, h->tv.p, vbn, cudaMemcpyDeviceToDevice, st));
+  int recomb = o.recombination;
+  if (recomb == OV_RECOMB_AUTO) {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    const size_t need = vbn * (size_t)(ktarget + 1);
+    recomb = need + ((size_t)2 << 30) < fr ? OV_RECOMB_STORED : OV_RECOMB_TWO_PASS;
+  }
+  // t_1 = x (unnormalised, nv_1 = ||x||) goes to basis slot 0 (stored mode) or ring slot 1;
+  // tw_1 = x to the w ring's slot 1; the zeroed ring slots 0 are t_0 = tw_0 = 0
+  std::vector<void*> slots;  // device pointer of each stored t_j (stored mode): slots[i] = t_{i+1}
+  if (recomb == OV_RECOMB_STORED) {
+    void* s0 = nullptr;
+    rc = basis_slot(h, vbn, 0, &s0);
+    if (rc == OV_OK) slots.push_back(s0);
+    else if (o.recombination == OV_RECOMB_AUTO) recomb = OV_RECOMB_TWO_PASS;
+    else return rc;
+  }
+  void* t1 = recomb == OV_RECOMB_STORED ? slots[0] : (char*)h->vring.p + vbn;
+  CK(launch_pack(h->prec, bt, xd, t1, herm ? nullptr : (char*)h->wring.p + vbn, c, (double*)h->partials.p,
+                 (unsigned*)h->counters.p, 1, h->scal.p, st));
   CK(cudaMemcpy2DAsync(h->scale.p, sizeof(double), (double*)c.nv + 1, sizeof(double) * ld, sizeof(double), nrhs,
                        cudaMemcpyDeviceToDevice, st));
   h->stats.launches += 1;
   h->stats.other_launches += 1;
   const int t_total = tstart(h, kClsTotal);
 
-  int recomb = o.recombination;
-  if (recomb == OV_RECOMB_AUTO) {
-    size_t fr = 0, tot = 0;
-    CK(cudaMemGetInfo(&fr, &tot));
-    const size_t need = vbn * (size_t)ktarget;
-    recomb = need + ((size_t)2 << 30) < fr ? OV_RECOMB_STORED : OV_RECOMB_TWO_PASS;
-  }
-
   StepArgs a{};
   a.b = bt;
   a.scal = h->scal.p;
-  a.tv = h->tv.p;
-  a.tw = h->tw.p;
   a.p = h->p.p;
   a.r = h->r.p;
   a.c = c;
@@ -669,7 +697,6 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   std::vector<double> estfin(nrhs, INFINITY), estin(nrhs, NAN);
   std::vector<int> dstatus(nrhs), dkbreak(nrhs), rhst(nrhs), rhit(nrhs), leff(nrhs);
   std::vector<double> eo(nrhs), ei(nrhs);
-  std::vector<void*> slots;  // device pointer of each stored v_j (stored mode)
   CK(cudaMemcpyAsync(h->cl.p, lreq.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(h->cc_fin.p, 0, sizeof(double2) * (size_t)nrhs * ld, st));
   CK(cudaMemsetAsync(h->cacc_fin.p, 0, acc_elem_bytes(h->prec) * (size_t)nrhs * ld, st));
@@ -688,7 +715,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     const int init[2] = {1, 0};
     CK(grow(h->jstate, sizeof(int) * 2));
     CK(cudaMemcpyAsync(h->jstate.p, init, sizeof(int) * 2, cudaMemcpyHostToDevice, st));
-    CK(grow(h->slot_tab, sizeof(void*) * (size_t)(ktarget + 1)));
+    CK(grow(h->slot_tab, sizeof(void*) * (size_t)(ktarget + 2)));
   }
   a.jdev = (int*)h->jstate.p;
   a.gticket = (unsigned*)((int*)h->jstate.p + 1);
@@ -696,7 +723,6 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   a.wring = h->wring.p;
   a.pool_bytes = vbn;
   a.slot_tab = recomb == OV_RECOMB_STORED ? (void* const*)h->slot_tab.p : nullptr;
-  CK(cudaMemsetAsync((char*)h->wring.p + vbn, 0, vbn, st));
   const int gU = (o.timing || o.graph_steps <= 0) ? 0 : o.graph_steps;
   // relaxed steps (double-float handles): float hopping from step relax_from on, the
   // same step in both passes
@@ -708,30 +734,40 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   }
   auto step_prec = [&](int jj) { return jj >= relax_from ? kPrecDF64Relaxed : h->prec; };
   int jdone = 0;
+  size_t slots_on_device = 0;  // entries of the device slot table written so far
   // outer steps jfrom+1 .. jto: basis slots (stored mode), the autotuned block size at
   // step 1, whole graph units replayed and the rest launched one by one
   auto run_span = [&](int jfrom, int jto) -> int {
+      const Phase ph_steps("outer steps");
       // basis slots of the span (stored mode), uploaded to the device slot table
       if (recomb == OV_RECOMB_STORED) {
+        // slots up to index jto: the update of step jto writes t_{jto+1} there
         const size_t first_new = slots.size();
-        for (int jj = jfrom + 1; jj <= jto; ++jj) {
+        const size_t upload_from = std::min(first_new, slots_on_device);
+        for (int i = (int)slots.size(); i <= jto; ++i) {
           void* vc = nullptr;
-          rc = basis_slot(h, vbn, jj - 1, &vc);
+          rc = basis_slot(h, vbn, i, &vc);
           if (rc != OV_OK) {
             if (o.recombination != OV_RECOMB_AUTO) return rc;
-            // out of memory: fall back to the double pass; the ring slot that step jj reads
-            // as v_{jj-1} gets the last stored vector
+            // out of memory: fall back to the double pass from step jfrom + 1 on; the ring
+            // gets t_{jfrom+1} and t_{jfrom} (t_0 = 0 is already in ring slot 0)
             recomb = OV_RECOMB_TWO_PASS;
             a.slot_tab = nullptr;
-            if (jj >= 2) CK(cudaMemcpyAsync((char*)h->vring.p + vbn * (jj & 1), slots[jj - 2], vbn,
-                                            cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync((char*)h->vring.p + vbn * ((jfrom + 1) & 1), slots[jfrom], vbn,
+                               cudaMemcpyDeviceToDevice, st));
+            if (jfrom >= 1)
+              CK(cudaMemcpyAsync((char*)h->vring.p + vbn * (jfrom & 1), slots[jfrom - 1], vbn,
+                                 cudaMemcpyDeviceToDevice, st));
+            slots.resize(first_new);
             break;
           }
           slots.push_back(vc);
         }
-        if (slots.size() > first_new)
-          CK(cudaMemcpyAsync((void**)h->slot_tab.p + first_new, slots.data() + first_new,
-                             sizeof(void*) * (slots.size() - first_new), cudaMemcpyHostToDevice, st));
+        if (recomb == OV_RECOMB_STORED && slots.size() > upload_from) {
+          CK(cudaMemcpyAsync((void**)h->slot_tab.p + upload_from, slots.data() + upload_from,
+                             sizeof(void*) * (slots.size() - upload_from), cudaMemcpyHostToDevice, st));
+          slots_on_device = slots.size();
+        }
       }
       int jn = jfrom + 1;
       if (jn == 1 && tune) {
@@ -804,17 +840,23 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
       }
     return OV_OK;
   };
+  // j: the step the loop has reached (the last check's, or the end of the last span);
+  // jdone >= j: steps run so far, speculative steps run during a check included. The loop
+  // ends when every right-hand side is done or the step at ktarget has been checked, also
+  // where speculative steps already reached ktarget (then no step is run, only the check).
   for (;;) {
-    if (jdone >= ktarget || ndone >= nrhs) break;
+    if (j >= ktarget || ndone >= nrhs) break;
     const bool fixed_span = o.k_fixed > 0;
     int target = fixed_span ? ktarget : std::min(next_check, ktarget);
-    if (h->sizer_on && !fixed_span && jdone < kSizerSteps && ktarget > kSizerSteps + 1)
+    if (h->sizer_on && !fixed_span && j < kSizerSteps && ktarget > kSizerSteps + 1)
       target = std::min(target, kSizerSteps);
-    if (target <= jdone) target = jdone + 1;
-    rc = run_span(jdone, target);
-    if (rc != OV_OK) return rc;
-    jdone = target;
-    j = jdone;
+    if (target <= j) target = j + 1;
+    if (target > jdone) {
+      rc = run_span(jdone, target);
+      if (rc != OV_OK) return rc;
+      jdone = target;
+    }
+    j = target;
     const bool fixed = o.k_fixed > 0;
     if (h->sizer_on && !fixed && j == kSizerSteps && ktarget > kSizerSteps + 1) {
       // learned sizing: f = (Re alpha_1..6, Im alpha_1..6, beta_2..5) -> (log k*, log l*)
@@ -903,6 +945,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     for (int r = 0; r < nrhs; ++r) kcur[r] = (dstatus[r] != kStOK && dkbreak[r] > 0) ? std::min(dkbreak[r], j) : j;
     CK(cudaMemcpyAsync(h->ck.p, kcur.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, cs));
     CK(cudaMemcpyAsync(h->ckprev.p, kprev.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, cs));
+    const Phase ph_check("stopping check");
     bool regrow = false;
     do {
     regrow = false;
@@ -910,8 +953,17 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     const int ti = tstart(h, kClsInner, cs);
     // where a stop is likely, both Roberts-Higham sets (the inner estimate's too) in one
     // launch instead of a second round trip
-    const int phase = (likely_stop && !fixed) ? 0 : 1;
-    cudaError_t e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, ld, iw,
+    // (the non-nested check has no inner estimate to defer)
+    const int phase = (!o.nested || (likely_stop && !fixed)) ? 0 : 1;
+    cudaError_t e;
+    if (!o.nested) {
+      CK(grow(h->nn_scratch, nonnested_scratch_bytes(nrhs, *std::max_element(kcur.begin(), kcur.end()))));
+      e = run_nonnested(nrhs, kcur.data(), c.alp, c.bet, c.gam, c.nv, ld, o.rh_tol, o.rh_maxit, (double2*)h->cc_cur.p,
+                        ld, h->cacc_cur.p, h->prec, (double*)h->c_est_in.p, (const double2*)h->cc_prev.p, ld,
+                        (const int*)h->ckprev.p, (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p,
+                        h->nn_scratch.p, cs);
+    } else
+    e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, c.nv, ld, iw,
                               o.rh_tol, o.rh_maxit, o.inner_dl, (double2*)h->cc_cur.p, ld, h->cacc_cur.p, h->prec,
                               (double*)h->c_est_in.p, (const double2*)h->cc_prev.p, ld, (const int*)h->ckprev.p,
                               (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, phase, cs);
@@ -937,7 +989,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
       CK(cudaStreamSynchronize(cs));
     } else if (want_inner) {
       const int t2 = tstart(h, kClsInner, cs);
-      e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, ld, iw, o.rh_tol,
+      e = run_inner(nrhs, (const int*)h->ck.p, (const int*)h->cl.p, herm ? 1 : 0, c.alp, c.bet, c.gam, c.nv, ld, iw, o.rh_tol,
                     o.rh_maxit, o.inner_dl, (double2*)h->cc_cur.p, ld, h->cacc_cur.p, h->prec,
                     (double*)h->c_est_in.p, (const double2*)h->cc_prev.p, ld, (const int*)h->ckprev.p,
                     (double*)h->c_est_out.p, (int*)h->c_rhst.p, (int*)h->c_rhit.p, 2, cs);
@@ -1066,6 +1118,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   h->last_ld = ld;
   h->last_nrhs = nrhs;
   // recombination
+  const Phase ph_recomb("recombination");
   CK(cudaMemcpyAsync(h->ck.p, kfin.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
   const int tr = tstart(h, kClsRecomb);
   if (recomb == OV_RECOMB_STORED) {
@@ -1076,30 +1129,25 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     h->stats.launches += 1;
     h->stats.other_launches += 1;
   } else {
-    // second pass: regenerate v_j from the stored coefficients and accumulate y += c_j v_j
+    // second pass: regenerate t_j from the stored coefficients (ring of two: t_{j+1}
+    // overwrites t_{j-1}) and accumulate y += (c_j / nv_j) t_j
     const size_t ab = acc_elem_bytes(h->prec) * pool;
     CK(grow(h->yacc, ab));
     CK(cudaMemsetAsync(h->yacc.p, 0, ab, st));
-    CK(launch_pack(h->prec, bt, xd, h->tv.p, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, nullptr, st));
     CK(cudaMemsetAsync(h->vring.p, 0, 2 * vbn, st));
+    CK(launch_pack(h->prec, bt, xd, (char*)h->vring.p + vbn, nullptr, c, (double*)h->partials.p,
+                   (unsigned*)h->counters.p, 0, nullptr, st));
     StepArgs b = a;
     b.jdev = nullptr;  // the second pass runs from host-side step indices
     b.slot_tab = nullptr;
     b.yacc = h->yacc.p;
     b.cacc = h->cacc_fin.p;
-    void* tcur = h->tv.p;
-    void* tnxt = h->p.p;
-    void* vprev2 = (char*)h->vring.p + vbn;
     for (int jj = 1; jj <= kmax_used; ++jj) {
-      void* vc = (char*)h->vring.p + vbn * ((jj - 1) % 2);
       b.j = jj;
-      b.tv = tcur;
-      b.tnext = tnxt;
-      b.vprev = vprev2;
-      b.vcur = vc;
+      b.tc = (char*)h->vring.p + vbn * (jj & 1);
+      b.tn = (char*)h->vring.p + vbn * ((jj - 1) & 1);
+      b.tp = b.tn;
       CK(launch_step(step_prec(jj), kModeRegen, b, st));
-      std::swap(tcur, tnxt);
-      vprev2 = vc;
     }
     CK(launch_finish_acc(h->prec, bt, h->yacc.p, (const double*)h->scale.p, xd, add_x, yd, st));
     h->stats.launches += kmax_used + 2;
@@ -1163,7 +1211,8 @@ extern "C" int ov_wilson_apply(ov_handle* h, int nrhs, const void* x, void* y, i
     yd = (double2*)h->ycanon.p;
   }
   Coefs c = coefs(h, h->cap_ld);
-  CK(launch_pack(h->prec, bt, xd, h->tv.p, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, nullptr, st));
+  CK(launch_pack(h->prec, bt, xd, h->tv.p, nullptr, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, nullptr,
+                 st));
   StepArgs a{};
   a.b = bt;
   a.tv = h->tv.p;
@@ -1291,7 +1340,7 @@ extern "C" int ov_inner_sign(ov_handle* h, int count, int ld, const int* k, cons
   cudaMemcpyAsync(h->cl.p, lv.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st);
   InnerWork iw = inner_work(h);
   cudaError_t e = run_inner(count, (const int*)h->ck.p, (const int*)h->cl.p, hermitian ? 1 : 0, (double2*)dA.p,
-                            (double2*)dB.p, (double2*)dG.p, ldi, iw, h->o.rh_tol, h->o.rh_maxit, h->o.inner_dl,
+                            (double2*)dB.p, (double2*)dG.p, nullptr, ldi, iw, h->o.rh_tol, h->o.rh_maxit, h->o.inner_dl,
                             (double2*)h->cc_cur.p, ldi, nullptr, h->prec, (double*)h->c_est_in.p, nullptr, ldi,
                             nullptr, nullptr, (int*)h->c_rhst.p, (int*)h->c_rhit.p, 0, st);
   std::vector<double2> C((size_t)count * ldi);
@@ -1320,9 +1369,42 @@ extern "C" int ov_inner_sign(ov_handle* h, int count, int ld, const int* k, cons
 
 extern "C" int ov_rh_sign(ov_handle* h, int count, int m, const void* T, void* S, int* iters) {
   if (!h || count < 1 || m < 1 || !T || !S) return OV_ERR_ARG;
-  if (m > kMaxL) return OV_ERR_TOO_LARGE;
+  if (m > kMaxInnerK) return OV_ERR_TOO_LARGE;
   CK(cudaSetDevice(h->dev));
   cudaStream_t st = h->st;
+  if (m > kMaxL) {
+    // beyond one CTA's shared memory: Gauss-Jordan over global memory, FP64
+    const size_t mb = sizeof(double2) * (size_t)count * m * m;
+    Buf dT, dS, scr;
+    auto cleanup = [&]() {
+      release(dT);
+      release(dS);
+      release(scr);
+    };
+    if (grow(dT, mb) != cudaSuccess || grow(dS, mb) != cudaSuccess ||
+        grow(scr, rh_big_scratch_bytes(count, m)) != cudaSuccess) {
+      cleanup();
+      return OV_ERR_NOMEM;
+    }
+    std::vector<int> it(count), ok(count);
+    cudaError_t e = cudaMemcpyAsync(dT.p, T, mb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = run_rh_big(count, m, (const double2*)dT.p, (double2*)dS.p, it.data(), ok.data(), h->o.rh_tol, h->o.rh_maxit,
+                     scr.p, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S, dS.p, mb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) {
+      fprintf(stderr, "libov: ov_rh_sign: %s\n", cudaGetErrorString(e));
+      return OV_ERR_CUDA;
+    }
+    int worst = OV_OK;
+    for (int i = 0; i < count; ++i) {
+      if (iters) iters[i] = it[i];
+      if (!ok[i]) worst = OV_ERR_RH_NOCONV;
+    }
+    return worst;
+  }
   int rc = ensure_inner(h, (count + 1) / 2, std::max(h->inner_ld, 4));
   if (rc != OV_OK) return rc;
   const size_t mb = sizeof(double2) * (size_t)count * m * m;

@@ -972,7 +972,8 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_df(const int* __restric
 // ------------------------------------------------------------ combine
 __global__ void __launch_bounds__(kInnerThreads) k_combine(int count, const int* __restrict__ k_dev,
                                                            const int* __restrict__ l_dev, InnerWork w, int dl,
-                                                           double2* c, int ldo, void* cacc, int prec,
+                                                           double2* c, int ldo, void* cacc, const double* nv,
+                                                           int ldn, int prec,
                                                            double* est_inner, const double2* cprev, int ldp,
                                                            const int* kprev_dev, double* est_outer, int* rh_status,
                                                            int* rh_iters, int have_est) {
@@ -1010,10 +1011,13 @@ __global__ void __launch_bounds__(kInnerThreads) k_combine(int count, const int*
     }
     c[(size_t)prob * ldo + m + 1] = v;
     if (cacc) {
+      // the recombination sums c_j v_j = (c_j / nv_j) t_j over the unnormalised basis
+      const double sc = nv ? 1.0 / nv[(size_t)prob * ldn + m + 1] : 1.0;
+      const double2 vs = make_double2(v.x * sc, v.y * sc);
       if (prec == OV_PREC_FP64) {
-        ((double2*)cacc)[(size_t)prob * ldo + m + 1] = v;
+        ((double2*)cacc)[(size_t)prob * ldo + m + 1] = vs;
       } else {
-        const df64 re = df_from_double(v.x), im = df_from_double(v.y);
+        const df64 re = df_from_double(vs.x), im = df_from_double(vs.y);
         ((float4*)cacc)[(size_t)prob * ldo + m + 1] = make_float4(re.hi, re.lo, im.hi, im.lo);
       }
     }
@@ -1046,8 +1050,9 @@ __global__ void __launch_bounds__(kInnerThreads) k_combine(int count, const int*
 static size_t inner_smem(int k) { return (size_t)13 * k * sizeof(double2) + 32 * sizeof(double) + k + 16; }
 
 cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermitian, const double2* alp,
-                      const double2* bet, const double2* gam, int ldc, InnerWork& w, double rh_tol, int rh_maxit,
-                      int inner_dl, double2* c, int ldo, void* cacc, int prec, double* est_inner,
+                      const double2* bet, const double2* gam, const double* nv, int ldc, InnerWork& w,
+                      double rh_tol, int rh_maxit, int inner_dl, double2* c, int ldo, void* cacc, int prec,
+                      double* est_inner,
                       const double2* cprev, int ldp, const int* kprev_dev, double* est_outer, int* rh_status,
                       int* rh_iters, int phase, cudaStream_t st) {
   cudaError_t e;
@@ -1093,8 +1098,8 @@ cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermiti
     k_rh<true><<<nmat, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit, mid0);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_combine<<<count, kInnerThreads, 0, st>>>(count, k_dev, l_dev, w, inner_dl, c, ldo, cacc, prec, est_inner, cprev,
-                                             ldp, kprev_dev, est_outer, rh_status, rh_iters, phase != 1);
+  k_combine<<<count, kInnerThreads, 0, st>>>(count, k_dev, l_dev, w, inner_dl, c, ldo, cacc, nv, ldc, prec, est_inner,
+                                             cprev, ldp, kprev_dev, est_outer, rh_status, rh_iters, phase != 1);
   return cudaGetLastError();
 }
 

@@ -63,34 +63,41 @@ struct Batch {
 
 // Arguments of one outer step (vector pointers are pools; problem r's vectors start at
 // desc[r].voff and are laid out [12][V] of the precision's storage type).
+//
+// The Krylov vectors are kept unnormalised: t_j = nv_j v_j on the v side and
+// tw_j = conj(nw_j) w_j on the w side, where nv_j, nw_j are the normalisations of the
+// recurrence (Sec. 2). The stored basis holds t_1 .. t_k, and 1/nv_j is folded into the
+// recurrence scalars and into the recombination coefficients, so no kernel writes the
+// normalised vectors.
 struct StepArgs {
   Batch b;
-  // per-problem step scalars in the arithmetic type of the precision (vec_t slots, [nprob][8]):
-  // 0: 1/nv_j, 1: gam_j, 2: 1/conj(nw_j), 3: conj(bet_j), 4: alpha_j, 5: conj(alpha_j).
-  // They are written once per step by the block that finalises the coefficient, so the
-  // site kernels do no double-precision work.
+  // per-problem step scalars in the arithmetic type of the precision (vec_t slots, [nprob][8]),
+  // written once per step by the block that finalises the coefficient (the site kernels do
+  // no double-precision work):
+  //   0: 1/nv_j                      1: c_v = gamma_j / nv_{j-1} (Lanczos: beta_j / nv_{j-1})
+  //   2: 1/conj(nw_j)                3: c_w = beta_j / conj(nw_{j-1})
+  //   4: alpha_j / nv_j              5: conj(alpha_j) / conj(nw_j)
   void* scal;
-  const void* tv;
-  const void* tw;
-  const void* vprev;
-  const void* wprev;
-  void* vcur;
-  void* wcur;
-  void* p;
-  void* r;
-  void* tnext;  // regeneration pass: next unnormalised vector
-  void* yacc;   // regeneration pass: y accumulator (accumulator type)
-  const void* cacc;  // regeneration pass: c_j in accumulator type, [nprob][ld]
+  const void* tv;  // apply mode: the source
+  void* p;         // A v_j - ..., and the apply mode's output
+  void* r;         // A^dag w_j - ...
+  // vectors of step j when jdev is NULL (the regeneration pass): t_j, t_{j-1} and the
+  // destination of t_{j+1} (which may alias t_{j-1})
+  const void* tc;
+  const void* tp;
+  void* tn;
+  void* yacc;        // regeneration pass: y accumulator (accumulator type)
+  const void* cacc;  // regeneration pass: c_j / nv_j in accumulator type, [nprob][ld]
   Coefs c;
   int j;
   // Device-side step state, so that a run of steps can be captured once in a CUDA graph
   // and replayed: when jdev is set the kernels take j from *jdev (the update kernel's last
-  // block advances it), v_j / v_{j-1} from the basis slot table (NULL: the two-slot ring
-  // vring, by parity of j) and w_j / w_{j-1} from the ring wring; otherwise they use the
-  // host fields j, vcur, vprev, wcur, wprev.
+  // block advances it) and their vectors from the basis slot table (slot i holds t_{i+1};
+  // t_0 is the zeroed ring slot 0) or, without a table, from the two-slot ring vring
+  // (t_j in slot j & 1; t_{j+1} overwrites t_{j-1}); the w side always uses the ring wring.
   int* jdev;
   unsigned* gticket;       // finished blocks of an update launch (global ticket)
-  void* const* slot_tab;   // device [k]: address of basis slot j-1 (v_j of every problem)
+  void* const* slot_tab;   // device [k + 1]: address of basis slot i (t_{i+1} of every problem)
   void* vring;
   void* wring;
   size_t pool_bytes;       // bytes of one vector of every problem (a slot)
@@ -104,8 +111,10 @@ void fill_consts(ProbDesc& d, double m_w, double mu);
 
 // outer-level launchers (ov_outer.cu); prec = OV_PREC_*. Canonical buffers hold, per
 // problem r, 12 V complex doubles at offset desc[r].voff (layout [V][12]).
-cudaError_t launch_pack(int prec, const Batch& b, const double2* xcanon, void* xint, Coefs c, double* partials,
-                        unsigned* counters, int want_norm, void* scal, cudaStream_t st);
+// x -> xint (and a copy to xint2 if not NULL); with want_norm the norms set nv_1 = nw_1 and
+// the step-1 scalars
+cudaError_t launch_pack(int prec, const Batch& b, const double2* xcanon, void* xint, void* xint2, Coefs c,
+                        double* partials, unsigned* counters, int want_norm, void* scal, cudaStream_t st);
 cudaError_t launch_unpack(int prec, const Batch& b, const void* xint, double2* ycanon, cudaStream_t st);
 cudaError_t launch_step(int prec, int mode, const StepArgs& a, cudaStream_t st);
 cudaError_t launch_update(int prec, int mode, const StepArgs& a, cudaStream_t st);
@@ -142,18 +151,33 @@ struct InnerWork {
 // arrays alp/bet/gam with leading dimension ldc (index j = 1..k as in Coefs, so the
 // diagonal is alp[j], the subdiagonal H_{j,j-1} = bet[j] and the superdiagonal
 // H_{j-1,j} = gam[j] for j >= 2). Results, index 1..k: c (double2 [count][ldo]) and, if
-// cacc is not NULL, c in the accumulator type of `prec`; est_inner[i]; est_outer[i]
+// cacc is not NULL, c_j / nv[j] (nv: the normalisations of the unnormalised basis vectors,
+// leading dimension ldc; NULL: 1) in the accumulator type of `prec`; est_inner[i]; est_outer[i]
 // against cprev (rows of length kprev[i], NULL: infinite); rh_status[i] (0 ok, 1 RH not
 // converged, 2 singular H); rh_iters[i]. phase 0: everything; phase 1: no inner estimate
 // (est_inner = NaN); phase 2: the inner estimate for the problems of a preceding phase-1
 // call (re-runs only the smaller Roberts-Higham set and the combination).
 cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermitian, const double2* alp,
-                      const double2* bet, const double2* gam, int ldc, InnerWork& w, double rh_tol,
-                      int rh_maxit, int inner_dl, double2* c, int ldo, void* cacc, int prec,
+                      const double2* bet, const double2* gam, const double* nv, int ldc, InnerWork& w,
+                      double rh_tol, int rh_maxit, int inner_dl, double2* c, int ldo, void* cacc, int prec,
                       double* est_inner, const double2* cprev, int ldp, const int* kprev_dev,
                       double* est_outer, int* rh_status, int* rh_iters, int phase, cudaStream_t st);
 cudaError_t run_rh_dense(int count, int m, const double2* T, double2* S, int* iters, int* ok,
                          double rh_tol, int rh_maxit, InnerWork& w, cudaStream_t st);
+
+// Roberts-Higham on large dense matrices and the non-nested stopping check (ov_rhbig.cu)
+size_t rh_big_scratch_bytes(int count, int k);
+// sgn of `count` dense k x k matrices T (device) into S (device); iters / ok: host arrays
+cudaError_t run_rh_big(int count, int k, const double2* T, double2* S, int* iters, int* ok, double rh_tol,
+                       int rh_maxit, void* scratch, cudaStream_t st);
+size_t nonnested_scratch_bytes(int count, int kmax);
+// the stopping check of the non-nested method: c = sgn(H_k) e_1 by Roberts-Higham on the
+// full H_k of each problem (k_host: host array of the problems' k); outputs as run_inner's
+// phase 0 (est_inner = 0: nothing is nested)
+cudaError_t run_nonnested(int count, const int* k_host, const double2* alp, const double2* bet, const double2* gam,
+                          const double* nv, int ldc, double rh_tol, int rh_maxit, double2* c, int ldo, void* cacc,
+                          int prec, double* est_inner, const double2* cprev, int ldp, const int* kprev_dev,
+                          double* est_outer, int* rh_status, int* rh_iters, void* scratch, cudaStream_t st);
 
 // learned sizing (ov_mlp.cu)
 cudaError_t mlp_predict_device(const float* theta_dev, int n, const float* X_dev, float* Y_dev, cudaStream_t st);

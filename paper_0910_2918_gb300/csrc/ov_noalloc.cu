@@ -21,6 +21,12 @@ namespace {
 
 constexpr int kNoAllocMaxCount = 64;  // matrices per call
 constexpr int kNoAllocThreads = 1024;
+// dynamic shared memory of one CTA: the m x m working matrix plus the column / reduction
+// buffer; at m = kMaxL it must fit the 227 KB a CTA may opt in to on sm_100-class GPUs
+constexpr size_t noalloc_smem(int m) {
+  return (size_t)m * m * sizeof(double2) + ((size_t)m * sizeof(double2) > 512 ? (size_t)m * sizeof(double2) : 512);
+}
+static_assert(noalloc_smem(kMaxL) <= 232448, "working matrix of the largest size exceeds 227 KB of shared memory");
 
 struct NoAllocScratch {
   int perm[kNoAllocMaxCount][kMaxL];  // row interchanges of the current inversion
@@ -177,7 +183,12 @@ extern "C" int ov_rh_sign_noalloc(int count, int m, const void* T, void* S, int*
   NoAllocScratch* scr = scratch_for_current_device();
   if (!scr) return OV_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t smem = (size_t)m * m * sizeof(double2) + std::max<size_t>((size_t)m * sizeof(double2), 512);
+  const size_t smem = noalloc_smem(m);
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return OV_ERR_CUDA;
+  if (smem > (size_t)optin) return OV_ERR_TOO_LARGE;
   if (cudaFuncSetAttribute(k_rh_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return OV_ERR_CUDA;
   k_rh_noalloc<<<count, kNoAllocThreads, smem, st>>>(m, (const double2*)T, (double2*)S, scr, rh_tol, rh_maxit);

@@ -94,14 +94,20 @@ template <class P>
 __device__ __forceinline__ void st_scal(void* scal, int r, int q, double re, double im) {
   st_vec((typename P::vec_t*)scal + (size_t)r * 8 + q, cd_to<typename P::R>(re, im));
 }
-// scalars of the next step from its coefficients (run by one thread)
+// scalars of step j from its coefficients nv_j, gamma_j, nw_j, beta_j and the previous
+// normalisations nv_{j-1}, nw_{j-1} (run by one thread):
+//   1/nv_j, gamma_j/nv_{j-1}, 1/conj(nw_j), conj(beta_j)/conj(nw_{j-1})
 template <class P>
-__device__ __forceinline__ void set_step_scal(void* scal, int r, double nv, double2 gam, double2 nw, double2 bet) {
+__device__ __forceinline__ void set_step_scal(void* scal, int r, double nv, double2 gam, double2 nw, double2 bet,
+                                              double nvp, double2 nwp) {
   st_scal<P>(scal, r, 0, 1.0 / nv, 0.0);
-  st_scal<P>(scal, r, 1, gam.x, gam.y);
+  st_scal<P>(scal, r, 1, gam.x / nvp, gam.y / nvp);
   const double den = nw.x * nw.x + nw.y * nw.y;
   st_scal<P>(scal, r, 2, nw.x / den, nw.y / den);  // 1/conj(nw) = nw/|nw|^2
-  st_scal<P>(scal, r, 3, bet.x, -bet.y);
+  // conj(beta)/conj(nwp) = conj(beta/nwp), beta/nwp = beta conj(nwp)/|nwp|^2
+  const double dp = nwp.x * nwp.x + nwp.y * nwp.y;
+  const double qr = (bet.x * nwp.x + bet.y * nwp.y) / dp, qi = (bet.y * nwp.x - bet.x * nwp.y) / dp;
+  st_scal<P>(scal, r, 3, qr, -qi);
 }
 
 // ------------------------------------------------------------ block reductions
@@ -216,8 +222,8 @@ __device__ __forceinline__ SiteRef site_ref(const Batch& b) {
 // ------------------------------------------------------------ pack / unpack
 template <class P, int BS>
 __global__ void __launch_bounds__(BS) k_pack(Batch bt, const double2* __restrict__ x, typename P::vec_t* xi,
-                                                 Coefs c, double* partials, unsigned* counters, int want_norm,
-                                                 void* scal) {
+                                                 typename P::vec_t* xi2, Coefs c, double* partials,
+                                                 unsigned* counters, int want_norm, void* scal) {
   using R = typename P::R;
   const SiteRef sr = site_ref<BS>(bt);
   const int s = sr.s, r = sr.r;
@@ -227,11 +233,13 @@ __global__ void __launch_bounds__(BS) k_pack(Batch bt, const double2* __restrict
   if (sr.active) {
     const double2* src = x + voff + (size_t)s * 12;
     typename P::vec_t* dst = xi + voff + s;
+    typename P::vec_t* dst2 = xi2 ? xi2 + voff + s : nullptr;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       double2 z = src[k];
       n2 = fma(z.x, z.x, fma(z.y, z.y, n2));
       st_vec(dst + (size_t)k * V, cd_to<R>(z.x, z.y));
+      if (dst2) st_vec(dst2 + (size_t)k * V, cd_to<R>(z.x, z.y));
     }
   }
   if (!want_norm) return;
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(BS) k_pack(Batch bt, const double2* __restrict
     c.gam[o] = make_double2(0.0, 0.0);
     c.status[r] = nrm > 0.0 ? kStOK : kStZero;
     c.kbreak[r] = 0;
-    if (scal) set_step_scal<P>(scal, r, c.nv[o], c.gam[o], c.nw[o], c.bet[o]);
+    if (scal) set_step_scal<P>(scal, r, c.nv[o], c.gam[o], c.nw[o], c.bet[o], 1.0, make_double2(1.0, 0.0));
   }
 }
 
@@ -582,41 +590,50 @@ __device__ __forceinline__ cx<df64> smulsub(cx<df64> s, cx<df64> q, cx<df64> c, 
     return {df_axpy2(-(w.re * c.re), s.re, q.re, -s.im, q.im), df_axpy2(-(w.im * c.re), s.re, q.im, s.im, q.re)};
   return smul<false>(s, q) - smul<false>(c, w);
 }
-// v_j = scl psi and out = scl (gamma5 D psi) - cf prev at one site, 12 components; the
-// alpha partial: Lanczos v_j^dag out, two-sided side w: w_j^dag p (p from side v)
+// out = scl (gamma5 D t_j) - cf t_{j-1} at one site, 12 components, with t_j the
+// unnormalised current vector (psi) and t_{j-1} the previous one; the alpha partial: Lanczos
+// t_j^dag out, two-sided side w: tw_j^dag p (p from side v); the finaliser divides by the
+// normalisation
 template <bool RS, bool RC, int DOT, class R, class VT, class AT>
-__device__ __forceinline__ void step_site(const VT* src, const VT* prv, VT* cur, VT* out, const VT* pp, int V, int s,
+__device__ __forceinline__ void step_site(const VT* src, const VT* prv, VT* out, const VT* pp, int V, int s,
                                           cx<R> scl, cx<R> cf, const cx<R> (&acc)[12], R mass, cx<AT>& dot) {
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const cx<R> psi = ld_vec(src + (size_t)k * V + s);
-    const cx<R> cv = smul<RS>(scl, psi);
     const cx<R> ok = smulsub<RS, RC>(scl, g5d(k, psi, acc[k], mass), cf, ld_vec(prv + (size_t)k * V));
-    st_vec(cur + (size_t)k * V, cv);
     st_vec(out + (size_t)k * V, ok);
-    if (DOT == 1) acc_dot(dot, cv, ok);
-    if (DOT == 2) acc_dot(dot, cv, ld_vec(pp + (size_t)k * V));
+    if (DOT == 1) acc_dot(dot, psi, ok);
+    if (DOT == 2) acc_dot(dot, psi, ld_vec(pp + (size_t)k * V));
   }
 }
 
-// the step index and the step's vector slots (device-side state or host fields)
+// the step index and the step's vectors (device-side state or host fields): t_j, t_{j-1},
+// the destination of t_{j+1}, and the same three on the w side
 struct StepPtrs {
   int j;
-  const void* vprev;
-  void* vcur;
-  const void* wprev;
-  void* wcur;
+  const void* tc;
+  const void* tp;
+  void* tn;
+  const void* wc;
+  const void* wp;
+  void* wn;
 };
 __device__ __forceinline__ StepPtrs step_ptrs(const StepArgs& a) {
-  if (!a.jdev) return {a.j, a.vprev, a.vcur, a.wprev, a.wcur};
+  if (!a.jdev) return {a.j, a.tc, a.tp, a.tn, nullptr, nullptr, nullptr};
   const int j = __ldcg(a.jdev);
   char* vr = (char*)a.vring;
   char* wr = (char*)a.wring;
   const size_t pb = a.pool_bytes;
-  void* vcur = a.slot_tab ? a.slot_tab[j - 1] : (void*)(vr + pb * ((j - 1) & 1));
-  const void* vprev = a.slot_tab ? (j == 1 ? (const void*)(vr + pb) : (const void*)a.slot_tab[j - 2])
-                                 : (const void*)(vr + pb * (j & 1));
-  return {j, vprev, vcur, wr + pb * (j & 1), wr + pb * ((j - 1) & 1)};
+  char* wc = wr + pb * (j & 1);
+  char* wp = wr + pb * ((j - 1) & 1);
+  if (a.slot_tab) {
+    // stored basis: slot i holds t_{i+1}; t_0 is the zeroed ring slot 0
+    const void* tp = j == 1 ? (const void*)vr : (const void*)a.slot_tab[j - 2];
+    return {j, a.slot_tab[j - 1], tp, a.slot_tab[j], wc, wp, wp};
+  }
+  char* tc = vr + pb * (j & 1);
+  char* tp = vr + pb * ((j - 1) & 1);
+  return {j, tc, tp, tp, wc, wp, wp};
 }
 
 // Register caps of the step kernels (the warps they add hide the load latency at the start
@@ -625,12 +642,24 @@ __device__ __forceinline__ StepPtrs step_ptrs(const StepArgs& a) {
 // of bytes and run slower), 85 for the relaxed step (24 warps; it fits in 80: 0.50 ->
 // 0.46 ms) and 64 for the float step (32 warps, a few spilled words: 0.32 -> 0.27 ms).
 // FP64 keeps the compiler's choice.
+// Resident threads per SM each step kernel is compiled for (the register cap follows:
+// 65536 / threads); overridable at build time to measure other splits.
+#ifndef OV_STEP_THREADS_DF64
+#define OV_STEP_THREADS_DF64 512
+#endif
+#ifndef OV_STEP_THREADS_DF64R
+#define OV_STEP_THREADS_DF64R 768
+#endif
+#ifndef OV_STEP_THREADS_F32
+#define OV_STEP_THREADS_F32 1024
+#endif
 template <class P, int BS>
 constexpr int step_min_blocks() {
-  return P::id == PrecDF64::id    ? 512 / BS
-         : P::id == PrecDF64R::id ? 768 / BS
-         : P::id == PrecF32::id   ? 1024 / BS
-                                  : 1;
+  constexpr int t = P::id == PrecDF64::id    ? OV_STEP_THREADS_DF64
+                    : P::id == PrecDF64R::id ? OV_STEP_THREADS_DF64R
+                    : P::id == PrecF32::id   ? OV_STEP_THREADS_F32
+                                             : BS;
+  return t / BS > 0 ? t / BS : 1;
 }
 
 template <class P, int MODE, int BS>
@@ -658,10 +687,10 @@ __global__ void __launch_bounds__(BS, step_min_blocks<P, BS>()) k_step(StepArgs 
 
   cx<A> dot = {rzero<A>(), rzero<A>()};
   cx<R> acc[12];
-  const V_t* tv = (const V_t*)a.tv + vo;
 
   if (MODE == kModeApply) {
     if (active) {
+      const V_t* tv = (const V_t*)a.tv + vo;
       hopping<P>(acc, tv, links, g, s, xc, a.dagger ? emui : emu, a.dagger ? emu : emui);
       V_t* out = (V_t*)a.p + vo + s;
 #pragma unroll
@@ -670,66 +699,80 @@ __global__ void __launch_bounds__(BS, step_min_blocks<P, BS>()) k_step(StepArgs 
     return;
   }
 
+  const V_t* tc = (const V_t*)sp.tc + vo;
   if (MODE == kModeRegen) {
-    // v_j = tv / nv_j ; p = A v_j - gam_j v_{j-1} ; all coefficients are known, so the
-    // update t_{j+1} = p - alpha_j v_j and the accumulation y += c_j v_j are fused here
+    // second pass, all coefficients known: p = A t_j / nv_j - (gamma_j / nv_{j-1}) t_{j-1},
+    // t_{j+1} = p - (alpha_j / nv_j) t_j (over t_{j-1}: each thread reads its own entry of
+    // t_{j-1} before writing it), and y += (c_j / nv_j) t_j
     if (!active) return;
-    const R rinv = from_double<R>(1.0 / a.c.nv[co]);
+    const double nvj = a.c.nv[co];
+    const double nvp = sp.j > 1 ? a.c.nv[co - 1] : 1.0;
+    const R rinv = from_double<R>(1.0 / nvj);
     const double2 gj = a.c.gam[co];
-    const cx<R> gam_j = cd_to<R>(gj.x, gj.y);
-    hopping<P>(acc, tv, links, g, s, xc, emu, emui);
-    const V_t* vp = (const V_t*)sp.vprev + vo + s;
-    V_t* vc = (V_t*)sp.vcur + vo + s;
+    const cx<R> cg = cd_to<R>(gj.x / nvp, gj.y / nvp);
     const double2 aj = a.c.alp[co];
-    const cx<R> alp_j = cd_to<R>(aj.x, aj.y);
+    const cx<R> ca = cd_to<R>(aj.x / nvj, aj.y / nvj);
+    hopping<P>(acc, tc, links, g, s, xc, emu, emui);
+    const V_t* tp = (const V_t*)sp.tp + vo + s;
+    V_t* tn = (V_t*)sp.tn + vo + s;
     const cx<AT> cjv = ld_acc((const AS*)a.cacc + (size_t)r * a.c.ld + sp.j);
-    V_t* tn = (V_t*)a.tnext + vo + s;
     AS* ya = (AS*)a.yacc + vo + s;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const cx<R> psi = ld_vec(tv + (size_t)k * g.V + s);
-      const cx<R> v = cscale(psi, rinv);
-      const cx<R> pk = cscale(g5d(k, psi, acc[k], mass), rinv) - cmul(gam_j, ld_vec(vp + (size_t)k * g.V));
-      st_vec(vc + (size_t)k * g.V, v);
-      st_vec(tn + (size_t)k * g.V, pk - cmul(alp_j, v));
+      const cx<R> psi = ld_vec(tc + (size_t)k * g.V + s);
+      const cx<R> pk = cscale(g5d(k, psi, acc[k], mass), rinv) - cmul(cg, ld_vec(tp + (size_t)k * g.V));
+      st_vec(tn + (size_t)k * g.V, pk - cmul(ca, psi));
       cx<AT> y = ld_acc(ya + (size_t)k * g.V);
-      acc_axpy(y, cjv, v);
+      acc_axpy(y, cjv, psi);
       st_acc(ya + (size_t)k * g.V, y);
     }
     return;
   }
 
   // Lanczos: one side (v). Two-sided: side 0 is v with A, side 1 is w with A^dag.
-  //   v_j = tv / nv_j,        p = A v_j - gam_j v_{j-1}
-  //   w_j = tw / conj(nw_j),  r = A^dag w_j - conj(bet_j) w_{j-1}
-  //   alpha_j = v_j^dag p (Lanczos) or w_j^dag p (two-sided)
+  //   p = A t_j / nv_j - (gamma_j / nv_{j-1}) t_{j-1}
+  //   r = A^dag tw_j / conj(nw_j) - (conj(beta_j) / conj(nw_{j-1})) tw_{j-1}
+  //   alpha_j = t_j^dag p / nv_j (Lanczos) or tw_j^dag p / nw_j (two-sided)
   const int nsides = MODE == kModeTwoSided ? 2 : 1;
 #pragma unroll 1
   for (int side = 0; side < nsides; ++side) {
     const cx<R> scl = ld_scal<P>(a.scal, r, 2 * side);
     const cx<R> cf = ld_scal<P>(a.scal, r, 2 * side + 1);
     if (active) {
-      const V_t* src = side == 0 ? tv : (const V_t*)a.tw + vo;
+      const V_t* src = side == 0 ? tc : (const V_t*)sp.wc + vo;
       hopping<P>(acc, src, links, g, s, xc, side == 0 ? emu : emui, side == 0 ? emui : emu);
-      const V_t* prv = side == 0 ? (const V_t*)sp.vprev + vo + s : (const V_t*)sp.wprev + vo + s;
-      V_t* cur = side == 0 ? (V_t*)sp.vcur + vo + s : (V_t*)sp.wcur + vo + s;
+      const V_t* prv = side == 0 ? (const V_t*)sp.tp + vo + s : (const V_t*)sp.wp + vo + s;
       V_t* out = side == 0 ? (V_t*)a.p + vo + s : (V_t*)a.r + vo + s;
       const V_t* pp = (const V_t*)a.p + vo + s;
       if (MODE == kModeLanczos)
-        step_site<true, true, 1>(src, prv, cur, out, pp, g.V, s, scl, cf, acc, mass, dot);
+        step_site<true, true, 1>(src, prv, out, pp, g.V, s, scl, cf, acc, mass, dot);
       else if (side == 0)
-        step_site<true, false, 0>(src, prv, cur, out, pp, g.V, s, scl, cf, acc, mass, dot);
+        step_site<true, false, 0>(src, prv, out, pp, g.V, s, scl, cf, acc, mass, dot);
       else
-        step_site<false, true, 2>(src, prv, cur, out, pp, g.V, s, scl, cf, acc, mass, dot);
+        step_site<false, false, 2>(src, prv, out, pp, g.V, s, scl, cf, acc, mass, dot);
     }
   }
   A v2[2] = {dot.re, dot.im};
   double tot[2];
   if (reduce_last<2, BS>(v2, a.partials, a.counters, r, d.block0, sr.bx, d.nblk, tot) && threadIdx.x == 0) {
-    const double ai = MODE == kModeLanczos ? 0.0 : tot[1];
-    a.c.alp[co] = make_double2(tot[0], ai);
-    st_scal<P>(a.scal, r, 4, tot[0], ai);
-    st_scal<P>(a.scal, r, 5, tot[0], -ai);
+    const double nvj = a.c.nv[co];
+    double ar, ai;
+    double2 nw = a.c.nw[co];
+    if (MODE == kModeLanczos) {
+      ar = tot[0] / nvj;
+      ai = 0.0;
+      nw = make_double2(nvj, 0.0);
+    } else {
+      // (tot) / nw_j
+      const double den = nw.x * nw.x + nw.y * nw.y;
+      ar = (tot[0] * nw.x + tot[1] * nw.y) / den;
+      ai = (tot[1] * nw.x - tot[0] * nw.y) / den;
+    }
+    a.c.alp[co] = make_double2(ar, ai);
+    // alpha_j / nv_j and conj(alpha_j) / conj(nw_j) = conj(alpha_j / nw_j)
+    st_scal<P>(a.scal, r, 4, ar / nvj, ai / nvj);
+    const double dw = nw.x * nw.x + nw.y * nw.y;
+    st_scal<P>(a.scal, r, 5, (ar * nw.x + ai * nw.y) / dw, -((ai * nw.x - ar * nw.y) / dw));
   }
 }
 
@@ -752,9 +795,10 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
   A nvv = rzero<A>();              // ||v~||^2: beta in Lanczos
   NL nvl = NL(0), nwl = NL(0);     // ||v~||^2, ||w~||^2 for the breakdown test of 2sL
   if (sr.active) {
+    // t_{j+1} = p - (alpha_j / nv_j) t_j, tw_{j+1} = r - (conj(alpha_j) / conj(nw_j)) tw_j
     const V_t* __restrict__ pp = (const V_t*)a.p + vo + s;
-    const V_t* __restrict__ vc = (const V_t*)sp.vcur + vo + s;
-    V_t* __restrict__ tv = (V_t*)a.tv + vo + s;  // written: the stencil no longer reads it
+    const V_t* __restrict__ vc = (const V_t*)sp.tc + vo + s;
+    V_t* __restrict__ tv = (V_t*)sp.tn + vo + s;  // may be t_{j-1}: the stencil no longer reads it
     if (MODE == kModeLanczos) {
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
@@ -764,8 +808,8 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       }
     } else {
       const V_t* __restrict__ rr = (const V_t*)a.r + vo + s;
-      const V_t* __restrict__ wc = (const V_t*)sp.wcur + vo + s;
-      V_t* __restrict__ tw = (V_t*)a.tw + vo + s;
+      const V_t* __restrict__ wc = (const V_t*)sp.wc + vo + s;
+      V_t* __restrict__ tw = (V_t*)sp.wn + vo + s;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         const cx<R> t = csubmul(ld_vec(pp + (size_t)k * g.V), alp, ld_vec(vc + (size_t)k * g.V));
@@ -795,7 +839,7 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       a.c.nw[cn] = make_double2(dead ? 1.0 : b, 0.0);
       a.c.bet[cn] = make_double2(dead ? 0.0 : b, 0.0);
       a.c.gam[cn] = make_double2(dead ? 0.0 : b, 0.0);
-      set_step_scal<P>(a.scal, r, a.c.nv[cn], a.c.gam[cn], a.c.nw[cn], a.c.bet[cn]);
+      set_step_scal<P>(a.scal, r, a.c.nv[cn], a.c.gam[cn], a.c.nw[cn], a.c.bet[cn], a.c.nv[co], a.c.nw[co]);
     }
   } else {
     A v4[4] = {d.re, d.im, to_acc(nvl, A()), to_acc(nwl, A())};
@@ -815,7 +859,7 @@ __global__ void __launch_bounds__(BS) k_update(StepArgs a) {
       a.c.nw[cn] = dead ? make_double2(1.0, 0.0) : make_double2(dre / b, dim / b);
       a.c.bet[cn] = make_double2(dead ? 0.0 : b, 0.0);
       a.c.gam[cn] = dead ? make_double2(0.0, 0.0) : make_double2(dre / b, dim / b);
-      set_step_scal<P>(a.scal, r, a.c.nv[cn], a.c.gam[cn], a.c.nw[cn], a.c.bet[cn]);
+      set_step_scal<P>(a.scal, r, a.c.nv[cn], a.c.gam[cn], a.c.nw[cn], a.c.bet[cn], a.c.nv[co], a.c.nw[co]);
     }
   }
   // device-side step state: the last block of the launch advances j
@@ -923,10 +967,11 @@ void fill_consts(ProbDesc& d, double m_w, double mu) {
     default: { constexpr int BS = 128; CALL; break; }      \
   }
 
-cudaError_t launch_pack(int prec, const Batch& b, const double2* x, void* xi, Coefs c, double* partials,
+cudaError_t launch_pack(int prec, const Batch& b, const double2* x, void* xi, void* xi2, Coefs c, double* partials,
                         unsigned* counters, int want_norm, void* scal, cudaStream_t st) {
   OV_BS_DISPATCH(b.block, OV_DISPATCH(prec, (k_pack<P, BS><<<b.nblocks, BS, 0, st>>>(
-                                                b, x, (typename P::vec_t*)xi, c, partials, counters, want_norm, scal))));
+                                                b, x, (typename P::vec_t*)xi, (typename P::vec_t*)xi2, c, partials,
+                                                counters, want_norm, scal))));
   return cudaGetLastError();
 }
 

@@ -63,29 +63,42 @@ def test_autotuned_block_size_changes_only_rounding(ov):
     assert ys[0][1] in (64, 128, 256)
 
 
-def test_batch_48_mixed_vs_oracle_sampled(ov):
+def test_batch_48_mixed_vs_oracle(ov):
     """The 48-problem workload (uneven lattices, Haar or near-unit links, mu in [0, 0.5])
-    in float arithmetic: every problem converges (or reports it), and sampled problems
-    agree with the FP64 oracle within the float bound."""
+    in float arithmetic, checks at 100 then every 25 steps: every problem that converges
+    is within 1e-6 of the FP64 path (itself within 1e-10 of the oracle), and one Haar
+    lattice of each shape plus a near-unit 8^4 lattice are within 1e-6 of the oracle.
+    The stopping estimate compares c_k with c_{k-25}; on the slowly converging Haar
+    lattices it undershoots the error by up to ~4x, so the float form stops at 1e-7 for
+    its 1e-6 bar (stopping at 5e-7 left 8 of 47 lattices between 1e-6 and 2.2e-6)."""
     probs = oi.problem_batch_48()
     Us = [oi.gauge_field(p["dims"], p["kind"], p["gauge_seed"], eps=p["eps"]) for p in probs]
     xs = [oi.gaussian_source(p["dims"], p["source_seed"]).reshape(1, -1) for p in probs]
-    hb = ov.ov_batch_create([p["dims"] for p in probs], Us, [p["m_w"] for p in probs], [p["mu"] for p in probs],
-                            "fp32", opts=ov.make_opts(check_interval=10))
-    try:
-        ys = [np.zeros_like(x) for x in xs]
-        rc, infos = ov.ov_batch_sign_apply(hb, xs, ys, 1e-6, 1000, 100)
-    finally:
-        ov.ov_destroy(hb)
-    assert all(i["status"] in (0, 1) for i in infos)
-    assert sum(i["status"] == 0 for i in infos) >= 40
-    for i in (1, 14, 27, 40):  # one of each lattice shape, near-unit links
+    args = ([p["dims"] for p in probs], Us, [p["m_w"] for p in probs], [p["mu"] for p in probs])
+    out = {}
+    for prec, stop, ob in (("fp32", 1e-7, dict(check_interval=25, first_check=100)),
+                           ("fp64", 1e-10, dict(check_interval=10))):
+        hb = ov.ov_batch_create(*args, prec, opts=ov.make_opts(**ob))
+        try:
+            ys = [np.zeros_like(x) for x in xs]
+            rc, infos = ov.ov_batch_sign_apply(hb, xs, ys, stop, 1000, 100)
+        finally:
+            ov.ov_destroy(hb)
+        out[prec] = (ys, infos)
+    (y32, i32), (y64, i64) = out["fp32"], out["fp64"]
+    assert all(i["status"] in (0, 1) for i in i32)
+    conv = [i for i in range(48) if i32[i]["status"] == 0 and i64[i]["status"] == 0]
+    assert len(conv) >= 40
+    errs = {i: rel(y32[i][0], y64[i][0]) for i in conv}
+    assert max(errs.values()) < 1e-6, sorted(errs.items(), key=lambda e: -e[1])[:4]
+    picks = [next(i for i in conv if i // 12 == s and probs[i]["kind"] == "haar") for s in range(4)]
+    picks.append(next(i for i in conv if i // 12 == 3 and probs[i]["kind"] == "near_unit"))
+    for i in picks:
         p = probs[i]
-        if infos[i]["status"] != 0:
-            continue
         yo, io = oracle_sign(links_for("fp32", Us[i]), p["dims"], p["m_w"], p["mu"], xs[i][0], k_max=1000,
                              l=100, tol=1e-9, check_interval=20)
-        assert rel(ys[i][0], yo) < 1e-5
+        assert io["status"] == 0
+        assert rel(y32[i][0], yo) < 1e-6, (i, rel(y32[i][0], yo))
 
 
 @pytest.mark.parametrize("mu", [0.0, 0.25])

@@ -52,6 +52,34 @@ def test_training_fits_a_smooth_map(ov):
     assert np.array_equal(theta, theta2)
 
 
+def test_adam_training_matches_oracle_steps(ov):
+    """Three full-batch epochs of the GPU training loop (forward, backward and Adam
+    kernels, beta 0.9 / 0.999, eps 1e-8) from a fixed theta equal three oracle steps
+    (loss_grad, then adam_step with t = 1, 2, 3) element by element. At t = 1 Adam moves
+    every parameter by about lr; at t = 2, 3 the bias corrections and both moments shape
+    the step, so a wrong beta or correction moves theta by O(lr) = 1e-2, far above the
+    bound. The bound, 1e-6 absolute plus 1e-5 relative, is ~15x the float-vs-double
+    difference of the same three steps computed in numpy float32 (7e-8)."""
+    rng = np.random.default_rng(5)
+    theta0 = (omlp.init_params(3) * 0.5).astype(np.float32)
+    X = rng.standard_normal((96, 16)).astype(np.float32)
+    Y = rng.standard_normal((96, 2)).astype(np.float32)
+    lr = 1e-2
+    theta, hist = ov.ov_mlp_train(theta0, X, Y, epochs=3, batch=0, lr=lr, seed=1)
+    th = theta0.astype(np.float64)
+    m, v = np.zeros_like(th), np.zeros_like(th)
+    for t in (1, 2, 3):
+        _, g = omlp.loss_grad(th, X.astype(np.float64), Y.astype(np.float64))
+        th, m, v = omlp.adam_step(th, g, m, v, t, lr)
+    d = np.abs(theta.astype(np.float64) - th)
+    assert np.all(d <= 1e-6 + 1e-5 * np.abs(th)), (float(d.max()), int(np.argmax(d)))
+    # every parameter with a nonzero gradient moved by about lr at t = 1
+    assert np.abs(th - theta0).max() > 2 * lr
+    # the reported loss is the loss of the returned parameters
+    assert omlp.loss(theta.astype(np.float64), X.astype(np.float64), Y.astype(np.float64)) == pytest.approx(
+        float(hist[-1]), rel=1e-4)
+
+
 def _constant_predictor(k_pred, l_pred):
     """Zero weights with biases (log k, log l): predicts the same (k, l) for every input."""
     th = np.zeros(5378, dtype=np.float32)

@@ -1,0 +1,96 @@
+"""The non-nested method (Sec. 2): Roberts-Higham on the full k x k Ritz matrix, the
+comparison point of the paper's nested method (Sec. 3). Large dense Roberts-Higham
+(m > 120: Gauss-Jordan over global memory) and whole applies with opts.nested = 0 against
+the oracle's roberts_higham / nonnested_sign_e1 / sign_apply(nested=False)."""
+import numpy as np
+import pytest
+
+import ovinputs as oi
+from gpu_util import oracle_sign, rel
+from oracle import krylov
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ov():
+    import paper_0910_2918_gb300 as ov
+
+    return ov
+
+
+def _matrices(rng, count, m):
+    """Non-normal complex matrices with eigenvalues away from the imaginary axis."""
+    mats = []
+    for _ in range(count):
+        X = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+        X = X + 4 * np.sqrt(m) * np.eye(m)  # keep the eigenvector matrix well conditioned
+        ev = np.concatenate([rng.uniform(0.2, 3, m // 2), -rng.uniform(0.2, 3, m - m // 2)])
+        ev = ev + 1j * rng.uniform(-1, 1, m)
+        mats.append(X @ np.diag(ev) @ np.linalg.inv(X))
+    return np.ascontiguousarray(np.stack(mats))
+
+
+@pytest.mark.parametrize("m,count", [(121, 3), (150, 2), (400, 2)])
+def test_large_roberts_higham_vs_oracle(ov, m, count):
+    T = _matrices(np.random.default_rng(m), count, m)
+    dims = (2, 2, 2, 2)
+    h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0)
+    try:
+        rc, S, its = ov.ov_rh_sign(h, T)
+    finally:
+        ov.ov_destroy(h)
+    assert rc == 0
+    for i in range(count):
+        So, ito, ok = krylov.roberts_higham(T[i])
+        assert ok
+        assert rel(S[i], So) < 1e-10, (i, rel(S[i], So))
+        assert abs(int(its[i]) - ito) <= 1
+        # sgn(T)^2 = 1 and [sgn(T), T] = 0 (the definition, independent of the oracle)
+        assert np.linalg.norm(S[i] @ S[i] - np.eye(m)) < 1e-8 * m
+        assert np.linalg.norm(S[i] @ T[i] - T[i] @ S[i]) < 1e-9 * np.linalg.norm(T[i])
+
+
+def test_large_roberts_higham_reports_singular(ov):
+    T = np.zeros((1, 130, 130), dtype=np.complex128)
+    T[0, :129, :129] = np.eye(129)
+    dims = (2, 2, 2, 2)
+    h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0)
+    try:
+        rc, S, its = ov.ov_rh_sign(h, T)
+    finally:
+        ov.ov_destroy(h)
+    assert rc == ov.binding.OV_ERR_RH_NOCONV
+
+
+@pytest.mark.parametrize("mu,k", [(0.0, 150), (0.3, 150), (0.3, 400)])
+def test_nonnested_apply_vs_oracle(ov, mu, k):
+    """A whole apply with opts.nested = 0 at fixed k: y = ||x|| V_k sgn(H_k) e_1 (Sec. 2,
+    Eq. (approximation) with Eq. (Roberts) on H_k) against the oracle's non-nested run."""
+    dims = (4, 4, 4, 4)
+    U = oi.gauge_field(dims, "haar", 0)
+    x = oi.gaussian_source(dims, 1)
+    y = np.zeros((1, x.size), dtype=np.complex128)
+    with ov.Overlap(dims, U, -1.5, mu, "fp64", opts=ov.make_opts(k_fixed=k, nested=0)) as op:
+        rc, info = op.sign_apply(x.reshape(1, -1).copy(), y, 0.0, k, 120)
+    assert rc == 0 and info[0]["k"] == k
+    yo, io = oracle_sign(U, dims, -1.5, mu, x, k_max=k, l=120, tol=0, k_fixed=k, nested=False)
+    assert rel(y[0], yo) < 1e-10, rel(y[0], yo)
+
+
+def test_nonnested_stopping_rule_and_nested_agree(ov):
+    """With the stopping rule, the non-nested and nested applies (l large enough for the
+    inner level to converge) reach the same answer; the non-nested run reports no inner
+    error."""
+    dims = (4, 4, 4, 4)
+    U = oi.gauge_field(dims, "near_unit", 3, eps=0.4)
+    x = oi.gaussian_source(dims, 4).reshape(1, -1)
+    out = {}
+    for nested in (0, 1):
+        y = np.zeros_like(x)
+        with ov.Overlap(dims, U, -1.5, 0.3, "fp64", opts=ov.make_opts(check_interval=10, nested=nested)) as op:
+            rc, info = op.sign_apply(x, y, 1e-10, 400, 120)
+        assert rc == 0
+        out[nested] = (y, info[0])
+    assert out[0][1]["err_inner"] == 0.0
+    assert rel(out[0][0][0], out[1][0][0]) < 1e-9

@@ -85,6 +85,26 @@ def test_c2_two_sided_8444_fixed_k(ov):
     assert rel(y[0], yo) < 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_c2_two_sided_stopping_rule_8444(ov, prec):
+    """The 8^4 workload whole: near-unit links exp(i 0.4 H), mu = 0.3, m_w = -1.5, one
+    Gaussian source, tol 1e-10, k <= 800, l = 100, a check every 10 steps, against the
+    oracle's own stopping run (it stops at k = 310). The stop is a threshold decision on
+    an estimate carrying roundoff, so the two may stop one check apart (the estimate at
+    k = 300 sits at 1e-10 while the answer there is 3.8e-10 from the one at k = 310);
+    the GPU answer is then compared with the oracle run to the GPU's own k."""
+    dims = (8, 8, 8, 8)
+    U = oi.gauge_field(dims, "near_unit", 0, eps=0.4)
+    x = oi.gaussian_source(dims, 1)
+    rc, y, info = gpu_sign(ov, dims, U, -1.5, 0.3, x, prec, 1e-10, 800, 100, check_interval=10)
+    yo, io = oracle_sign(U, dims, -1.5, 0.3, x, k_max=800, l=100, tol=1e-10, check_interval=10)
+    assert rc == 0 and info[0]["status"] == 0 and io["status"] == 0
+    assert abs(info[0]["k"] - io["k"]) <= 10
+    if info[0]["k"] != io["k"]:
+        yo, io = oracle_sign(U, dims, -1.5, 0.3, x, k_max=800, l=100, tol=0, k_fixed=info[0]["k"])
+    assert rel(y[0], yo) < 1e-10, (info[0]["k"], io["k"], rel(y[0], yo))
+
+
 def test_free_field_closed_form(ov):
     dims = (4, 4, 4, 8)
     U = oi.gauge_field(dims, "unit", 0)
@@ -256,3 +276,71 @@ def test_overlapped_checks_equal_serial_order(ov, mu):
     assert [i["err_est"] for i in i0] == [i["err_est"] for i in i1]
     assert [i["status"] for i in i1] == [0] * 4
     assert np.array_equal(y0, y1)
+
+
+def test_final_check_runs_when_speculative_steps_reach_k_max(ov):
+    """A check 5 steps before k_max lets speculative steps (run while the check is
+    evaluated) reach k_max; the step at k_max must still be checked and the result
+    recombined there: k = k_max, status OV_NOT_CONVERGED at an unreachable tol, and y
+    equal to the oracle at the same fixed k (it once came back empty with k = 0)."""
+    dims = (4, 4, 4, 4)
+    U = oi.gauge_field(dims, "near_unit", 2, eps=0.4)
+    x = oi.gaussian_source(dims, 3)
+    k_max, l = 80, 80  # l_eff = k: the inner level is exact, parity holds at any k
+    for mu in (0.0, 0.3):
+        rc, y, info = gpu_sign(ov, dims, U, -1.5, mu, x, "fp64", 1e-14, k_max, l, check_interval=25,
+                               first_check=k_max - 5, overlap_checks=1)
+        assert info[0]["k"] == k_max and rc == 1 and info[0]["status"] == 1
+        yo, io = oracle_sign(U, dims, -1.5, mu, x, k_max=k_max, l=l, tol=0, k_fixed=k_max)
+        assert rel(y[0], yo) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_serious_breakdown_returns_the_error(ov, prec):
+    """A serious breakdown of two-sided Lanczos (|w~^dag v~| <= breakdown_tol ||v~|| ||w~||),
+    forced from the host with a huge threshold: the call returns OV_ERR_BREAKDOWN at the
+    first check (no hang, the handle stays usable), as the oracle reports it at step 1."""
+    dims = (4, 4, 4, 4)
+    U = oi.gauge_field(dims, "near_unit", 2, eps=0.4)
+    x = oi.gaussian_source(dims, 3)
+    with ov.Overlap(dims, U, -1.5, 0.3, prec, opts=ov.make_opts(breakdown_tol=1e6)) as op:
+        y = np.zeros((1, x.size), dtype=np.complex128)
+        with pytest.raises(ov.OvError) as e:
+            op.sign_apply(x.reshape(1, -1).copy(), y, 1e-10, 200, 60)
+        assert e.value.code == ov.binding.OV_ERR_BREAKDOWN
+        # the same handle still works with the default threshold
+        op.set_opts(breakdown_tol=1e-14, k_fixed=40)
+        rc, info = op.sign_apply(x.reshape(1, -1).copy(), y, 1e-10, 40, 40)
+        assert rc == 0 and info[0]["k"] == 40
+    fA, fAH = (lambda v: dirac.A_apply(U, v, dims, -1.5, 0.3)), (lambda v: dirac.AH_apply(U, v, dims, -1.5, 0.3))
+    out = krylov.Outer(fA, fAH, x, False, breakdown_tol=1e6)
+    out.step()
+    assert out.status == krylov.ERR_BREAKDOWN
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_auto_recombination_falls_back_to_the_double_pass(ov, monkeypatch, mu):
+    """OV_RECOMB_AUTO stores the basis while device memory lasts; when a basis allocation
+    fails mid-run (here: a cap of one 64-step chunk, injected through OV_BASIS_CAP_BYTES)
+    the run continues in the double pass and the answer equals the stored one."""
+    dims = (4, 4, 4, 4)
+    U = oi.gauge_field(dims, "near_unit", 4, eps=0.4)
+    x = oi.gaussian_source(dims, 5).reshape(1, -1)
+    k = 150
+    pool = 12 * 256 * 16  # one FP64 vector of the 4^4 lattice, bytes
+    ys, stats = {}, {}
+    for mode, cap in (("stored", None), ("auto_capped", 64 * pool + 1)):
+        if cap is None:
+            monkeypatch.delenv("OV_BASIS_CAP_BYTES", raising=False)
+        else:
+            monkeypatch.setenv("OV_BASIS_CAP_BYTES", str(cap))
+        recomb = 0 if mode == "stored" else 2
+        y = np.zeros_like(x)
+        with ov.Overlap(dims, U, -1.5, mu, "fp64", opts=ov.make_opts(k_fixed=k, recombination=recomb)) as op:
+            rc, info = op.sign_apply(x, y, 0.0, k, 100)
+            stats[mode] = op.stats()
+        assert rc == 0 and info[0]["k"] == k
+        ys[mode] = y
+    monkeypatch.delenv("OV_BASIS_CAP_BYTES", raising=False)
+    assert stats["stored"]["regen_steps"] == 0 and stats["auto_capped"]["regen_steps"] == k
+    assert rel(ys["auto_capped"][0], ys["stored"][0]) < 1e-12

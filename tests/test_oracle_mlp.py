@@ -44,3 +44,30 @@ def test_adam_first_step_is_signed_lr():
     g = np.array([0.3, -2.0, 1e-3])
     th, m, v = mlp.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01, eps=0.0)
     assert np.allclose(th, -0.01 * np.sign(g))
+
+
+def test_adam_three_steps_hand_computed():
+    """Steps t = 1, 2, 3 of Adam (Kingma & Ba 2015, Algorithm 1) on two parameters, with
+    beta1 = 1/2, beta2 = 3/4, lr = 1/10, eps = 1/100, worked out by hand in exact fractions:
+
+      parameter 0, gradients 2, 4, -2, theta_0 = 1:
+        t=1: m = 1,    v = 1,      m^ = 2,    v^ = 4
+        t=2: m = 5/2,  v = 19/4,   m^ = 10/3, v^ = 76/7
+        t=3: m = 1/4,  v = 73/16,  m^ = 2/7,  v^ = 292/37
+      parameter 1, gradients -1, 3, 1/2, theta_0 = -1/2:
+        t=1: m = -1/2, v = 1/4,    m^ = -1,   v^ = 1
+        t=2: m = 5/4,  v = 39/16,  m^ = 5/3,  v^ = 39/7
+        t=3: m = 7/8,  v = 121/64, m^ = 1,    v^ = 121/37
+      theta_t = theta_{t-1} - lr m^ / (sqrt(v^) + eps).
+    beta1 and beta2 differ and the bias corrections 1 - beta^t change with t, so swapping
+    the betas, dropping a correction or using the wrong power fails at t = 2 or 3."""
+    expect = {1: [0.900497512437811, -0.400990099009901],
+              2: [0.7996407712601878, -0.47130209453229205],
+              3: [0.7895063677291949, -0.526295832219544]}
+    grads = {1: [2.0, -1.0], 2: [4.0, 3.0], 3: [-2.0, 0.5]}
+    th, m, v = np.array([1.0, -0.5]), np.zeros(2), np.zeros(2)
+    for t in (1, 2, 3):
+        th, m, v = mlp.adam_step(th, np.array(grads[t]), m, v, t, lr=0.1, beta1=0.5, beta2=0.75, eps=0.01)
+        assert np.allclose(th, expect[t], rtol=0, atol=1e-14), (t, th)
+    assert np.allclose(m, [0.25, 0.875], rtol=0, atol=1e-15)
+    assert np.allclose(v, [73 / 16, 121 / 64], rtol=0, atol=1e-15)

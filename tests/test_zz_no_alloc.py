@@ -61,3 +61,37 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     with pytest.raises(ov.OvError) as e:
         ov.ov_rh_sign_noalloc(T, torch.zeros_like(T))
     assert e.value.code == -7
+
+
+def test_noalloc_reports_singular_and_iteration_cap():
+    """Status handling read back by the host: an exactly singular matrix (all zeros: the
+    first pivot is zero) and an iteration cap of 1 both return OV_ERR_RH_NOCONV, with the
+    iterations used reported (never more than the cap)."""
+    import torch
+
+    import paper_0910_2918_gb300 as ov
+
+    Z = torch.zeros((1, 8, 8), dtype=torch.complex128, device="cuda")
+    rc, its = ov.ov_rh_sign_noalloc(Z, torch.zeros_like(Z))
+    assert rc == ov.binding.OV_ERR_RH_NOCONV
+    assert 1 <= its[0] <= 100
+    T = torch.from_numpy(_matrices(np.random.default_rng(3), 2, 16)).cuda()
+    rc, its = ov.ov_rh_sign_noalloc(T, torch.zeros_like(T), rh_maxit=1)
+    assert rc == ov.binding.OV_ERR_RH_NOCONV
+    assert list(its) == [1, 1]
+
+
+def test_noalloc_binding_rejects_mismatched_buffers():
+    """The binding refuses buffers the kernel would read or write out of bounds."""
+    import torch
+
+    import paper_0910_2918_gb300 as ov
+
+    T = torch.zeros((2, 8, 6), dtype=torch.complex128, device="cuda")
+    with pytest.raises(ValueError):
+        ov.ov_rh_sign_noalloc(T, torch.zeros_like(T))
+    T = torch.zeros((2, 8, 8), dtype=torch.complex128, device="cuda")
+    with pytest.raises(ValueError):
+        ov.ov_rh_sign_noalloc(T, torch.zeros((1, 8, 8), dtype=torch.complex128, device="cuda"))
+    with pytest.raises(ValueError):
+        ov.ov_rh_sign_noalloc(T[0], torch.zeros_like(T[0]))
