@@ -204,6 +204,21 @@ int ov_sign_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, doubl
 int ov_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max,
              int l, ov_info* info);
 
+/* x_r = D(m)^{-1} b_r for nrhs right-hand sides (canonical layout, `mem` says where), with
+ * the massive overlap operator D(m) = (1 - m/2) D_ov(mu) + m (m = mass, 0 <= m < 2; m = 0 is
+ * D_ov itself, Sec. 1, Eq. (Dov)): the overlap operator inside an iterative solver.
+ * Conjugate gradients on the normal equations D^dag D x = D^dag b (CGNR), where
+ *   D v     = (1 - m/2) (v + gamma5 sgn(A) v) + m v,
+ *   D^dag v = (1 - m/2) (v + sgn(A^dag) gamma5 v) + m v,   A^dag = gamma5 D_w(-mu),
+ * each sign function a nested apply of this handle (its options, tolerance sign_tol,
+ * k_max, l). Stops when ||b_r - D x_r|| <= tol ||b_r|| (the recurrence's residual) for every
+ * right-hand side, else after maxit iterations (OV_NOT_CONVERGED). iters, resid: nrhs
+ * entries each (may be NULL): iterations used and final relative residual. The solver's
+ * work vectors (seven of nrhs x 12 V complex doubles) are allocated per call. Returns the
+ * worst status of the solve and of its sign applies. */
+int ov_solve(ov_handle* h, int nrhs, const void* b, void* x, int mem, double mass, double tol, int maxit,
+             double sign_tol, int k_max, int l, int* iters, double* resid);
+
 /* A batch of independent lattice problems of uneven sizes (one source each), advanced
  * together: every outer step is one launch over all problems' sites, and each check
  * runs the inner level of all problems together. geoms[i], links[i], m_w[i], mu[i]

@@ -24,6 +24,7 @@ from .binding import (  # noqa: F401
     ov_rh_sign_noalloc,
     ov_set_opts,
     ov_sign_apply,
+    ov_solve,
     ov_strerror,
     ov_version,
     ov_wilson_apply,

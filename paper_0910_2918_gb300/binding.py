@@ -111,6 +111,9 @@ def lib():
         f.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                       ctypes.POINTER(ov_info)]
         f.restype = ctypes.c_int
+    L.ov_solve.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                           ctypes.c_double, ctypes.c_int, ctypes.c_int, ip, dp]
+    L.ov_solve.restype = ctypes.c_int
     L.ov_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ov_geom), ctypes.POINTER(vp),
                                   ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ov_opts), vp]
@@ -273,6 +276,26 @@ def ov_sign_apply(h, x, y, tol, k_max, l):
 def ov_apply(h, x, y, tol, k_max, l):
     """y = D_ov(mu) x = x + gamma5 sgn(gamma5 D_w(mu)) x."""
     return _apply(lib().ov_apply, h, x, y, tol, k_max, l)
+
+
+def ov_solve(h, b, x, mass=0.0, tol=1e-8, maxit=200, sign_tol=1e-10, k_max=1000, l=120):
+    """x = D(m)^{-1} b, D(m) = (1 - m/2) D_ov + m, by CG on the normal equations; every
+    D and D^dag application is a nested sign apply. Returns (status, iterations, residuals)."""
+    _check_c128(b, "b")
+    _check_c128(x, "x")
+    nrhs = _nrhs(b)
+    bp, bm = _ptr_mem(b)
+    xp, xm = _ptr_mem(x, writable=True)
+    if bm != xm:
+        raise ValueError("b and x must both be host or both device arrays")
+    its = np.zeros(nrhs, dtype=np.int32)
+    res = np.zeros(nrhs, dtype=np.float64)
+    rc = lib().ov_solve(ctypes.c_void_p(h), nrhs, bp, xp, bm, float(mass), float(tol), int(maxit), float(sign_tol),
+                        int(k_max), int(l), its.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                        res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc < 0:
+        raise OvError(rc, "ov_solve")
+    return rc, its, res
 
 
 def ov_wilson_apply(h, x, y, dagger=False):
@@ -534,6 +557,9 @@ class Overlap:
 
     def apply(self, x, y, tol, k_max, l):
         return ov_apply(self.h, x, y, tol, k_max, l)
+
+    def solve(self, b, x, mass=0.0, tol=1e-8, maxit=200, sign_tol=1e-10, k_max=1000, l=120):
+        return ov_solve(self.h, b, x, mass, tol, maxit, sign_tol, k_max, l)
 
     def wilson_apply(self, x, y, dagger=False):
         return ov_wilson_apply(self.h, x, y, dagger)

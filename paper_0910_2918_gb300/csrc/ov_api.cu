@@ -214,7 +214,8 @@ extern "C" int ov_reset_stats(ov_handle* h) {
 // Problem descriptors of one call: problem r uses lattice lat_of[r]; vectors are pooled
 // (12 V_r complex entries per problem, in problem order). Uploads the descriptors and the
 // block map and returns the batch description and the pool size in complex entries.
-static int build_batch(ov_handle* h, const std::vector<int>& lat_of, int bs, Batch* b, size_t* pool) {
+static int build_batch(ov_handle* h, const std::vector<int>& lat_of, int bs, Batch* b, size_t* pool,
+                       int neg_mu = 0) {
   const int np = (int)lat_of.size();
   std::vector<ProbDesc> d(np);
   std::vector<int2> map;
@@ -225,7 +226,7 @@ static int build_batch(ov_handle* h, const std::vector<int>& lat_of, int bs, Bat
     const Lattice& L = h->lat[lat_of[r]];
     d[r].g = L.g;
     d[r].links = L.links.p;
-    fill_consts(d[r], L.m_w, L.mu);
+    fill_consts(d[r], L.m_w, neg_mu ? -L.mu : L.mu);
     d[r].voff = voff;
     d[r].block0 = blk;
     d[r].nblk = num_site_blocks(L.g, bs);
@@ -603,7 +604,7 @@ static int graph_for(ov_handle* h, const StepArgs& a, int prec, int mode, int U,
 
 // ---------------------------------------------------------------- sign apply
 static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,
-                           ov_info* info, int add_x) {
+                           ov_info* info, int add_x, int neg_mu = 0) {
   const Phase ph_apply("ov_sign_apply");
   if (!h || !x || !y || nrhs < 1 || k_max < 1 || l < 1 || !(tol >= 0.0)) return OV_ERR_ARG;
   if (mem != OV_MEM_HOST && mem != OV_MEM_DEVICE) return OV_ERR_ARG;
@@ -631,7 +632,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     if (it != h->tuned.end()) bs = it->second;
     else { bs = kBlockDefault; tune = true; }
   }
-  int rc = build_batch(h, lat_of, bs, &bt, &pool);
+  int rc = build_batch(h, lat_of, bs, &bt, &pool, neg_mu);
   if (rc != OV_OK) return rc;
   rc = ensure_outer(h, nrhs, ld, pool, max_blocks(h, lat_of));
   if (rc != OV_OK) return rc;
@@ -781,7 +782,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
         for (int cand : {64, 128, 256}) {
           Batch bc;
           size_t pc = 0;
-          rc = build_batch(h, lat_of, cand, &bc, &pc);
+          rc = build_batch(h, lat_of, cand, &bc, &pc, neg_mu);
           if (rc != OV_OK) return rc;
           a.b = bc;
           float tmin = 1e30f;
@@ -800,7 +801,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         h->tuned[key] = best_bs;
-        rc = build_batch(h, lat_of, best_bs, &bt, &pool);
+        rc = build_batch(h, lat_of, best_bs, &bt, &pool, neg_mu);
         if (rc != OV_OK) return rc;
         a.b = bt;
         if (h->trace) fprintf(stderr, "{\"ov_autotune\": %d, \"ms\": %.4f}\n", best_bs, best);
@@ -1174,6 +1175,23 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
     else if (worst == OV_OK && stat[r] > 0) worst = stat[r];
   }
   return worst;
+}
+
+// for the solver (ov_solve.cu): the sign function on device buffers, of A (neg_mu = 0) or
+// of A^dag = gamma5 D_w(-mu) (neg_mu = 1)
+int ov::sign_apply_device(ov_handle* h, int nrhs, const double2* x, double2* y, double tol, int k_max, int l,
+                          ov_info* info, int neg_mu) {
+  return sign_apply_impl(h, nrhs, x, y, OV_MEM_DEVICE, tol, k_max, l, info, 0, neg_mu);
+}
+cudaStream_t ov::handle_stream(const ov_handle* h) { return h->st; }
+int ov::handle_device(const ov_handle* h) { return h->dev; }
+size_t ov::handle_pool(const ov_handle* h, int nrhs) {
+  if (h->is_batch) {
+    size_t n = 0;
+    for (const Lattice& L : h->lat) n += 12 * (size_t)L.g.V;
+    return nrhs == (int)h->lat.size() ? n : 0;
+  }
+  return 12 * (size_t)h->lat[0].g.V * nrhs;
 }
 
 extern "C" int ov_sign_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,

@@ -179,6 +179,13 @@ cudaError_t run_nonnested(int count, const int* k_host, const double2* alp, cons
                           int prec, double* est_inner, const double2* cprev, int ldp, const int* kprev_dev,
                           double* est_outer, int* rh_status, int* rh_iters, void* scratch, cudaStream_t st);
 
+// host orchestration used by the solver (defined in ov_api.cu)
+int sign_apply_device(ov_handle* h, int nrhs, const double2* x, double2* y, double tol, int k_max, int l,
+                      ov_info* info, int neg_mu);
+cudaStream_t handle_stream(const ov_handle* h);
+int handle_device(const ov_handle* h);
+size_t handle_pool(const ov_handle* h, int nrhs);  // complex entries of nrhs vectors (0: not allowed)
+
 // learned sizing (ov_mlp.cu)
 cudaError_t mlp_predict_device(const float* theta_dev, int n, const float* X_dev, float* Y_dev, cudaStream_t st);
 int mlp_num_params();

@@ -65,8 +65,11 @@ struct BigWork {
   double2* S;      // [count][k][k] the iterate
   double2* W0;     // [count][k][k] elimination buffers (ping-pong)
   double2* W1;
-  double* pv;      // [count][nparts] partial maxima of the next pivot column
-  int* pi;         // [count][nparts] their rows
+  // partial maxima of a pivot column and their rows, [2][count][nparts]: launch j reads
+  // half j & 1 (written by launch j - 1, or the start for j = 0) and writes half
+  // (j + 1) & 1, so no block reads a value another block of its own launch writes
+  double* pv;
+  int* pi;
   int* used;       // [count][k] row already a pivot
   int* piv;        // [count][k] pivot row of column j
   int* status;     // [count] 0 running, 1 converged, 2 singular or not finite
@@ -110,12 +113,14 @@ __global__ void __launch_bounds__(kThreads) k_big_col(BigWork w, int j, const do
   if (w.status[mat] != 0) return;
   const size_t base = (size_t)mat * k * k;
   // the pivot: reduce the partial maxima of the previous launch (same order in every block)
+  const size_t half_in = (size_t)(j & 1) * w.count * w.nparts;
+  const size_t half_out = (size_t)((j + 1) & 1) * w.count * w.nparts;
   if (threadIdx.x < 32) {
     double v = -1.0;
     int i = 0x7fffffff;
     for (int q = threadIdx.x; q < w.nparts; q += 32) {
-      const double qv = w.pv[(size_t)mat * w.nparts + q];
-      const int qi = w.pi[(size_t)mat * w.nparts + q];
+      const double qv = w.pv[half_in + (size_t)mat * w.nparts + q];
+      const int qi = w.pi[half_in + (size_t)mat * w.nparts + q];
       if (qv > v || (qv == v && qi < i)) { v = qv; i = qi; }
     }
 #pragma unroll
@@ -170,7 +175,8 @@ __global__ void __launch_bounds__(kThreads) k_big_col(BigWork w, int j, const do
       if (a > bv) { bv = a; bi = i; }
     }
   }
-  block_argmax(bv, bi, sv, si, &w.pv[(size_t)mat * w.nparts + part], &w.pi[(size_t)mat * w.nparts + part]);
+  block_argmax(bv, bi, sv, si, &w.pv[half_out + (size_t)mat * w.nparts + part],
+               &w.pi[half_out + (size_t)mat * w.nparts + part]);
 }
 
 // S_{n+1} = (S_n + S_n^{-1}) / 2 with (S_n^{-1})_{i, p_m} = W_{p_i, m}; partial norms
@@ -243,7 +249,7 @@ __global__ void k_big_conv(BigWork w, double tol, int* its, int it) {
 size_t rh_big_scratch_bytes(int count, int k) {
   const int nparts = (k + kRows - 1) / kRows;
   const size_t mk = (size_t)count * k * k * sizeof(double2);
-  return 2 * mk + (size_t)count * nparts * (sizeof(double) * 3 + sizeof(int)) + (size_t)count * k * sizeof(int) * 3 +
+  return 2 * mk + (size_t)count * nparts * (sizeof(double) * 4 + sizeof(int) * 2) + (size_t)count * k * sizeof(int) * 3 +
          (size_t)count * sizeof(int) * 2 + 256 * 16;
 }
 
@@ -261,8 +267,8 @@ cudaError_t run_rh_big(int count, int k, const double2* T, double2* S, int* iter
   w.S = S;
   w.W0 = (double2*)take(mk);
   w.W1 = (double2*)take(mk);
-  w.pv = (double*)take(sizeof(double) * count * nparts);
-  w.pi = (int*)take(sizeof(int) * count * nparts);
+  w.pv = (double*)take(sizeof(double) * 2 * count * nparts);
+  w.pi = (int*)take(sizeof(int) * 2 * count * nparts);
   w.norms = (double*)take(sizeof(double) * 2 * count * nparts);
   w.used = (int*)take(sizeof(int) * count * k);
   w.piv = (int*)take(sizeof(int) * count * k);

@@ -63,12 +63,16 @@ def test_large_roberts_higham_reports_singular(ov):
     assert rc == ov.binding.OV_ERR_RH_NOCONV
 
 
-@pytest.mark.parametrize("mu,k", [(0.0, 150), (0.3, 150), (0.3, 400)])
-def test_nonnested_apply_vs_oracle(ov, mu, k):
+@pytest.mark.parametrize("kind,mu,k", [("haar", 0.0, 150), ("haar", 0.3, 150), ("near_unit", 0.3, 400)])
+def test_nonnested_apply_vs_oracle(ov, kind, mu, k):
     """A whole apply with opts.nested = 0 at fixed k: y = ||x|| V_k sgn(H_k) e_1 (Sec. 2,
-    Eq. (approximation) with Eq. (Roberts) on H_k) against the oracle's non-nested run."""
+    Eq. (approximation) with Eq. (Roberts) on H_k) against the oracle's non-nested run.
+    (On Haar links at mu = 0.3 the two-sided process has lost biorthogonality by k = 400:
+    a 1e-15 change of x moves the oracle's own result there by 1.8e-7, so no two
+    implementations agree to roundoff at that k, nested or not; near-unit links keep the
+    process stable to k = 400.)"""
     dims = (4, 4, 4, 4)
-    U = oi.gauge_field(dims, "haar", 0)
+    U = oi.gauge_field(dims, kind, 0, eps=0.4)
     x = oi.gaussian_source(dims, 1)
     y = np.zeros((1, x.size), dtype=np.complex128)
     with ov.Overlap(dims, U, -1.5, mu, "fp64", opts=ov.make_opts(k_fixed=k, nested=0)) as op:
