@@ -17,8 +17,11 @@ Modules
   exact   -- the spectral definition (Eq. (specdef)) for dense matrices, the
              Roberts-Higham iteration on a full dense matrix, and the
              closed-form free-field sign function through the FFT.
+  deflation -- the critical eigenpairs of a dense matrix and the deflated sign
+             function f(A)x = R f(Lambda) L^dag x + f(A)(I - R L^dag)x (Sec. 2).
+  mlp     -- the sizing network: forward, gradient, Adam (not in the paper).
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, exact identities or brute force; none is "parity unpinned".
 """
-from . import dirac, krylov, exact  # noqa: F401
+from . import dirac, krylov, exact, deflation  # noqa: F401
