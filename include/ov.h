@@ -219,6 +219,30 @@ int ov_apply(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol
 int ov_solve(ov_handle* h, int nrhs, const void* b, void* x, int mem, double mass, double tol, int maxit,
              double sign_tol, int k_max, int l, int* iters, double* resid);
 
+/* Deflation of the critical eigenvalues (Sec. 2, the deflation paragraph):
+ *   sgn(A) x = R_m sgn(Lambda_m) (L_m^dag x) + sgn(A) (I - R_m L_m^dag) x,
+ * with the m eigenvalues of A of smallest magnitude, their right eigenvectors R_m and left
+ * eigenvectors L_m (L_m^dag R_m = 1); sgn(lambda) = sgn(Re lambda). ov_deflate computes them
+ * on the device for every lattice of the handle and attaches them: from then on every
+ * apply of the handle (ov_sign_apply, ov_apply, ov_batch_sign_apply, ov_solve) deflates
+ * (m = 0 detaches). Eigensolver: subspace iteration on a block of 2 m + 8 vectors (at most 64) with
+ * a Chebyshev filter of degree 16 in A^2, Rayleigh-Ritz with A^2 on the block and with A on
+ * its leading m vectors, until every residual
+ * ||A r - lambda r|| <= tol ||A|| (maxit iterations at most); at mu != 0 a second run on
+ * A^dag gives the left eigenvectors. m <= 48 (OV_ERR_TOO_LARGE), 2 m + 8 <= 12 V. Only the
+ * pairs whose residual (right and left) is within tol are attached: the formula is exact
+ * for any set of true eigenpairs, and a poor pair would put its error into the exact part;
+ * the Krylov part then sees the spectrum with the attached ones removed. lam_out: 2 m
+ * doubles per lattice (re, im, all m computed; may be NULL); res_out: m doubles per lattice,
+ * their relative residuals (may be NULL); m_used: one int per lattice, the pairs attached
+ * (may be NULL). Returns OV_NOT_CONVERGED if fewer than m pairs were attached for a lattice.
+ * The handle owns the attached vectors (2 m_used of 12 V complex doubles per lattice). */
+int ov_deflate(ov_handle* h, int m, double tol, int maxit, double* lam_out, double* res_out, int* m_used);
+/* The deflation data of lattice `lattice` (0 for a single-field handle): up to mcap
+ * eigenvalues (complex doubles), right and left eigenvectors ([m][12 V] complex doubles,
+ * canonical layout), all HOST memory (any may be NULL); m receives their number. */
+int ov_get_deflation(const ov_handle* h, int lattice, int mcap, void* lam, void* R, void* L, int* m);
+
 /* A batch of independent lattice problems of uneven sizes (one source each), advanced
  * together: every outer step is one launch over all problems' sites, and each check
  * runs the inner level of all problems together. geoms[i], links[i], m_w[i], mu[i]

@@ -10,6 +10,8 @@ from .binding import (  # noqa: F401
     ov_batch_create,
     ov_batch_sign_apply,
     ov_create,
+    ov_deflate,
+    ov_get_deflation,
     ov_default_opts,
     ov_get_coefficients,
     ov_mlp_forward,

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libov.so")
-SOURCES = ["ov_outer.cu", "ov_inner.cu", "ov_api.cu", "ov_noalloc.cu", "ov_mlp.cu", "ov_rhbig.cu", "ov_solve.cu"]
+SOURCES = ["ov_outer.cu", "ov_inner.cu", "ov_api.cu", "ov_noalloc.cu", "ov_mlp.cu", "ov_rhbig.cu", "ov_solve.cu", "ov_eig.cu", "ov_small.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]

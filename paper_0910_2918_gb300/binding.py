@@ -111,6 +111,10 @@ def lib():
         f.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                       ctypes.POINTER(ov_info)]
         f.restype = ctypes.c_int
+    L.ov_deflate.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, ip]
+    L.ov_deflate.restype = ctypes.c_int
+    L.ov_get_deflation.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, ip]
+    L.ov_get_deflation.restype = ctypes.c_int
     L.ov_solve.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                            ctypes.c_double, ctypes.c_int, ctypes.c_int, ip, dp]
     L.ov_solve.restype = ctypes.c_int
@@ -296,6 +300,36 @@ def ov_solve(h, b, x, mass=0.0, tol=1e-8, maxit=200, sign_tol=1e-10, k_max=1000,
     if rc < 0:
         raise OvError(rc, "ov_solve")
     return rc, its, res
+
+
+def ov_deflate(h, m, tol=1e-10, maxit=200, nlat=1):
+    """Compute the m critical eigenpairs of every lattice and attach the converged ones
+    (m = 0 detaches). Returns (status, eigenvalues (nlat, m) complex, relative residuals
+    (nlat, m), pairs attached per lattice (nlat,))."""
+    lam = np.zeros(2 * max(m, 1) * nlat, dtype=np.float64)
+    res = np.zeros(max(m, 1) * nlat, dtype=np.float64)
+    used = np.zeros(nlat, dtype=np.int32)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib().ov_deflate(ctypes.c_void_p(h), int(m), float(tol), int(maxit), lam.ctypes.data_as(dp),
+                          res.ctypes.data_as(dp), used.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if rc < 0:
+        raise OvError(rc, "ov_deflate")
+    lam = (lam[0::2] + 1j * lam[1::2])[:m * nlat].reshape(nlat, m)
+    return rc, lam, res[:m * nlat].reshape(nlat, m), used
+
+
+def ov_get_deflation(h, lattice, mcap, n):
+    """(eigenvalues, R, L) of one lattice: R, L of shape (m, n) complex128 (host)."""
+    lam = np.zeros(max(mcap, 1), dtype=np.complex128)
+    R = np.zeros((max(mcap, 1), n), dtype=np.complex128)
+    L = np.zeros((max(mcap, 1), n), dtype=np.complex128)
+    m = ctypes.c_int(0)
+    rc = lib().ov_get_deflation(ctypes.c_void_p(h), int(lattice), int(mcap), lam.ctypes.data, R.ctypes.data,
+                                L.ctypes.data, ctypes.byref(m))
+    if rc != OV_OK:
+        raise OvError(rc, "ov_get_deflation")
+    k = m.value
+    return lam[:k], R[:k], L[:k]
 
 
 def ov_wilson_apply(h, x, y, dagger=False):
@@ -557,6 +591,14 @@ class Overlap:
 
     def apply(self, x, y, tol, k_max, l):
         return ov_apply(self.h, x, y, tol, k_max, l)
+
+    def deflate(self, m, tol=1e-10, maxit=200):
+        rc, lam, res, used = ov_deflate(self.h, m, tol, maxit)
+        return rc, lam[0], res[0]
+
+    def deflation(self, mcap=64):
+        n = 12 * int(np.prod(self.dims))
+        return ov_get_deflation(self.h, 0, mcap, n)
 
     def solve(self, b, x, mass=0.0, tol=1e-8, maxit=200, sign_tol=1e-10, k_max=1000, l=120):
         return ov_solve(self.h, b, x, mass, tol, maxit, sign_tol, k_max, l)

@@ -25,6 +25,7 @@
 #include <climits>
 
 #include <algorithm>
+#include <complex>
 #include <map>
 #include <vector>
 
@@ -138,6 +139,16 @@ struct ov_handle {
   int trace = 0;  // OV_TRACE set in the environment: one JSON line per check on stderr
   size_t basis_cap = 0;  // OV_BASIS_CAP_BYTES: bytes the stored basis may take (0: no cap)
   Buf nn_scratch;        // the non-nested check's dense H_k, iterates and elimination buffers
+  // deflation (Sec. 2): per lattice the critical eigenvalues and right / left eigenvectors
+  // (canonical complex doubles, [m][12 V]; L = R at mu = 0)
+  struct Defl {
+    int m = 0;
+    std::vector<std::complex<double>> lam;
+    std::vector<double> res;
+    Buf R, L;
+  };
+  std::vector<Defl> defl;
+  Buf dx, dy, dpart, dG;  // the deflated apply's source, result and coefficient scratch
   // event pairs recorded around timed launches: (class, start, stop)
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_class;
@@ -432,9 +443,14 @@ extern "C" void ov_destroy(ov_handle* h) {
                 &h->coef_kbreak, &h->partials, &h->counters, &h->scale, &h->scal, &h->iQ, &h->iT, &h->ileff, &h->iS, &h->is,
                 &h->irh_its, &h->irh_ok, &h->iperm, &h->ifail, &h->ck, &h->cl, &h->ckprev, &h->cc_cur, &h->cc_prev,
                 &h->cc_fin, &h->cacc_cur, &h->cacc_fin, &h->c_est_in, &h->c_est_out, &h->c_rhst, &h->c_rhit,
-                &h->vptr, &h->sizer_theta, &h->sizer_feat, &h->sizer_pred, &h->nn_scratch};
+                &h->vptr, &h->sizer_theta, &h->sizer_feat, &h->sizer_pred, &h->nn_scratch, &h->dx, &h->dy,
+                &h->dpart, &h->dG};
   for (Buf* b : all) release(*b);
   for (Buf& b : h->chunks) release(b);
+  for (auto& d : h->defl) {
+    release(d.R);
+    release(d.L);
+  }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (auto& gr : h->graphs)
     if (gr.exec) cudaGraphExecDestroy(gr.exec);
@@ -603,7 +619,7 @@ static int graph_for(ov_handle* h, const StepArgs& a, int prec, int mode, int U,
 }
 
 // ---------------------------------------------------------------- sign apply
-static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,
+static int sign_apply_core(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,
                            ov_info* info, int add_x, int neg_mu = 0) {
   const Phase ph_apply("ov_sign_apply");
   if (!h || !x || !y || nrhs < 1 || k_max < 1 || l < 1 || !(tol >= 0.0)) return OV_ERR_ARG;
@@ -1177,6 +1193,93 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   return worst;
 }
 
+// With deflation (Sec. 2): sgn(A) x = R sgn(Lambda) (L^dag x) + sgn(A) (I - R L^dag) x, the
+// second term by the Krylov path on the deflated source; for A^dag (neg_mu) the roles of R
+// and L swap (its eigenvalues are conj(lambda), with the same signs of the real parts).
+static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,
+                           ov_info* info, int add_x, int neg_mu = 0) {
+  bool any = false;
+  for (const auto& d : h ? h->defl : std::vector<ov_handle::Defl>{}) any = any || d.m > 0;
+  if (!h || !any || !x || !y || nrhs < 1) return sign_apply_core(h, nrhs, x, y, mem, tol, k_max, l, info, add_x, neg_mu);
+  if (mem != OV_MEM_HOST && mem != OV_MEM_DEVICE) return OV_ERR_ARG;
+  if (h->is_batch && nrhs != (int)h->lat.size()) return OV_ERR_ARG;
+  CK(cudaSetDevice(h->dev));
+  cudaStream_t st = h->st;
+  const std::vector<int> lat_of = lattices_of_call(h, nrhs);
+  size_t pool = 0;
+  for (int q : lat_of) pool += 12 * (size_t)h->lat[q].g.V;
+  const size_t vb = sizeof(double2) * pool;
+  CK(grow(h->dx, vb));
+  CK(grow(h->dy, vb));
+  const cudaMemcpyKind kin = mem == OV_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(h->dx.p, x, vb, kin, st));
+  // groups of consecutive right-hand sides on one lattice (a single-field handle: one group)
+  struct Grp {
+    int q, r0, nr;
+    size_t off;
+  };
+  std::vector<Grp> grps;
+  size_t off = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    const int q = lat_of[r];
+    if (!grps.empty() && grps.back().q == q && !h->is_batch) ++grps.back().nr;
+    else grps.push_back({q, r, 1, off});
+    off += 12 * (size_t)h->lat[q].g.V;
+  }
+  // c = L^dag x per group, x' = x - R c (into dy, the core's source)
+  std::vector<std::vector<double2>> coef(grps.size());
+  CK(cudaMemcpyAsync(h->dy.p, h->dx.p, vb, cudaMemcpyDeviceToDevice, st));
+  for (size_t g = 0; g < grps.size(); ++g) {
+    const Grp& G = grps[g];
+    const auto& d = h->defl.size() > (size_t)G.q ? h->defl[G.q] : ov_handle::Defl{};
+    if (d.m == 0) continue;
+    const size_t n = 12 * (size_t)h->lat[G.q].g.V;
+    const double2* Rv = (const double2*)(neg_mu ? d.L.p : d.R.p);
+    const double2* Lv = (const double2*)(neg_mu ? d.R.p : d.L.p);
+    CK(grow(h->dpart, block_gram_part_bytes(d.m, G.nr)));
+    CK(grow(h->dG, sizeof(double2) * (size_t)d.m * G.nr * 2));
+    double2* Gd = (double2*)h->dG.p;
+    const double2* xg = (const double2*)h->dx.p + G.off;
+    CK(block_gram(n, Lv, n, d.m, xg, n, G.nr, (double2*)h->dpart.p, Gd, st));
+    CK(block_mul(n, Rv, n, d.m, Gd, (double2*)h->dy.p + G.off, n, G.nr, -1.0, 1.0, st));
+    coef[g].resize((size_t)d.m * G.nr);
+    CK(cudaMemcpyAsync(coef[g].data(), Gd, sizeof(double2) * d.m * G.nr, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  // the Krylov part on the deflated source, in place in dy (its result overwrites it)
+  int rc = sign_apply_core(h, nrhs, h->dy.p, h->dx.p, OV_MEM_DEVICE, tol, k_max, l, info, 0, neg_mu);
+  if (rc < 0) return rc;
+  // y = y' + R sgn(Lambda) c  (and x + gamma5 (...) for the overlap operator)
+  for (size_t g = 0; g < grps.size(); ++g) {
+    const Grp& G = grps[g];
+    const auto& d = h->defl.size() > (size_t)G.q ? h->defl[G.q] : ov_handle::Defl{};
+    if (d.m == 0) continue;
+    const size_t n = 12 * (size_t)h->lat[G.q].g.V;
+    std::vector<double2> cs = coef[g];
+    for (int i = 0; i < d.m; ++i) {
+      const double sg = d.lam[i].real() >= 0.0 ? 1.0 : -1.0;
+      for (int r = 0; r < G.nr; ++r) {
+        cs[(size_t)i * G.nr + r].x *= sg;
+        cs[(size_t)i * G.nr + r].y *= sg;
+      }
+    }
+    double2* Gd = (double2*)h->dG.p + (size_t)d.m * G.nr;
+    CK(cudaMemcpyAsync(Gd, cs.data(), sizeof(double2) * cs.size(), cudaMemcpyHostToDevice, st));
+    const double2* Rv = (const double2*)(neg_mu ? d.L.p : d.R.p);
+    CK(block_mul(n, Rv, n, d.m, Gd, (double2*)h->dx.p + G.off, n, G.nr, 1.0, 1.0, st));
+    CK(cudaStreamSynchronize(st));  // cs is read by the copy before it goes out of scope
+  }
+  if (add_x) {
+    // the source again (dx holds the sign now): from the caller's buffer
+    CK(cudaMemcpyAsync(h->dy.p, x, vb, kin, st));
+    CK(add_x_gamma5(pool, (const double2*)h->dy.p, (double2*)h->dx.p, st));
+  }
+  const cudaMemcpyKind kout = mem == OV_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(y, h->dx.p, vb, kout, st));
+  CK(cudaStreamSynchronize(st));
+  return rc;
+}
+
 // for the solver (ov_solve.cu): the sign function on device buffers, of A (neg_mu = 0) or
 // of A^dag = gamma5 D_w(-mu) (neg_mu = 1)
 int ov::sign_apply_device(ov_handle* h, int nrhs, const double2* x, double2* y, double tol, int k_max, int l,
@@ -1184,6 +1287,186 @@ int ov::sign_apply_device(ov_handle* h, int nrhs, const double2* x, double2* y, 
   return sign_apply_impl(h, nrhs, x, y, OV_MEM_DEVICE, tol, k_max, l, info, 0, neg_mu);
 }
 cudaStream_t ov::handle_stream(const ov_handle* h) { return h->st; }
+size_t ov::lattice_size(const ov_handle* h, int q) { return 12 * (size_t)h->lat[q].g.V; }
+double ov::lattice_mu(const ov_handle* h, int q) { return h->lat[q].mu; }
+double ov::lattice_mass(const ov_handle* h, int q) { return h->lat[q].m_w + 4.0; }
+
+int ov::apply_block(ov_handle* h, int q, int b, const double2* X, double2* Y, int dagger) {
+  cudaStream_t st = h->st;
+  const std::vector<int> lat_of(b, q);
+  Batch bt;
+  size_t pool = 0;
+  int rc = build_batch(h, lat_of, h->o.block_size ? h->o.block_size : kBlockDefault, &bt, &pool);
+  if (rc != OV_OK) return rc;
+  rc = ensure_outer(h, b, std::max(h->cap_ld, 4), pool, max_blocks(h, lat_of));
+  if (rc != OV_OK) return rc;
+  Coefs c = coefs(h, h->cap_ld);
+  CK(launch_pack(h->prec, bt, X, h->tv.p, nullptr, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, nullptr,
+                 st));
+  StepArgs a{};
+  a.b = bt;
+  a.tv = h->tv.p;
+  a.p = h->p.p;
+  a.dagger = dagger ? 1 : 0;
+  a.c = c;
+  CK(launch_step(h->prec, kModeApply, a, st));
+  CK(launch_unpack(h->prec, bt, h->p.p, Y, st));
+  h->stats.launches += 3;
+  h->stats.stencil_launches += 1;
+  h->stats.other_launches += 2;
+  return OV_OK;
+}
+
+extern "C" int ov_deflate(ov_handle* h, int m, double tol, int maxit, double* lam_out, double* res_out, int* m_used) {
+  if (!h || m < 0 || !(tol > 0.0) || maxit < 1) return OV_ERR_ARG;
+  if (m > 48) return OV_ERR_TOO_LARGE;
+  CK(cudaSetDevice(h->dev));
+  const int nl = (int)h->lat.size();
+  h->defl.resize(nl);
+  int worst = OV_OK;
+  for (int q = 0; q < nl; ++q) {
+    auto& d = h->defl[q];
+    d.m = 0;
+    if (m_used) m_used[q] = 0;
+    if (m == 0) {
+      release(d.R);
+      release(d.L);
+      continue;
+    }
+    const size_t n = 12 * (size_t)h->lat[q].g.V;
+    if ((size_t)2 * m + 8 > n) return OV_ERR_ARG;
+    // a block of 2 m + 8 vectors: the filter's gap is between the m-th and the b-th eigenvalue
+    const int b = std::min<int>(64, 2 * m + 8);
+    const int deg = 16;
+    const bool herm = h->lat[q].mu == 0.0;
+    Buf R0, L0, tmp, part, g;
+    auto cleanup = [&]() {
+      for (Buf* bb : {&R0, &L0, &tmp, &part, &g}) release(*bb);
+    };
+    if (grow(R0, sizeof(double2) * n * m) != cudaSuccess || (!herm && grow(L0, sizeof(double2) * n * m) != cudaSuccess) ||
+        grow(tmp, sizeof(double2) * n * m) != cudaSuccess || grow(part, block_gram_part_bytes(m, m)) != cudaSuccess ||
+        grow(g, sizeof(double2) * m * m) != cudaSuccess) {
+      cleanup();
+      return OV_ERR_NOMEM;
+    }
+    std::vector<std::complex<double>> lam, lamL;
+    std::vector<double> res, resL;
+    int its = 0;
+    int rc = eig_smallest(h, q, 0, m, b, deg, tol, maxit, (double2*)R0.p, lam, res, &its, h->trace);
+    if (rc < 0) {
+      cleanup();
+      return rc;
+    }
+    std::vector<int> perm(m);
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    if (!herm) {
+      // left eigenvectors: right eigenvectors of A^dag for conj(lambda), matched by eigenvalue
+      int rc2 = eig_smallest(h, q, 1, m, b, deg, tol, maxit, (double2*)L0.p, lamL, resL, &its, h->trace);
+      if (rc2 < 0) {
+        cleanup();
+        return rc2;
+      }
+      std::vector<int> used(m, 0);
+      for (int i = 0; i < m; ++i) {
+        int best = 0;
+        double bd = INFINITY;
+        for (int j = 0; j < m; ++j) {
+          const double dd = std::abs(lamL[j] - std::conj(lam[i]));
+          if (!used[j] && dd < bd) { bd = dd; best = j; }
+        }
+        used[best] = 1;
+        perm[i] = best;
+        // a pair counts as converged only when both sides are and the eigenvalues agree
+        res[i] = std::max(std::max(res[i], resL[best]), bd / std::max(std::abs(lam[i]), 1e-300) * 1e-3);
+      }
+    }
+    // keep the converged pairs only: the deflation formula is exact for any set of true
+    // eigenpairs, while an inaccurate pair would put its error into the exact part
+    std::vector<int> keep;
+    for (int i = 0; i < m; ++i)
+      if (res[i] <= tol) keep.push_back(i);
+    const int mk = (int)keep.size();
+    if (mk < m) worst = OV_NOT_CONVERGED;
+    CK(grow(d.R, sizeof(double2) * n * std::max(mk, 1)));
+    CK(grow(d.L, sizeof(double2) * n * std::max(mk, 1)));
+    if (mk > 0) {
+      std::vector<double2> C((size_t)m * mk, make_double2(0.0, 0.0));
+      for (int c = 0; c < mk; ++c) C[(size_t)keep[c] * mk + c] = make_double2(1.0, 0.0);
+      cudaError_t e = cudaMemcpyAsync(g.p, C.data(), sizeof(double2) * m * mk, cudaMemcpyHostToDevice, h->st);
+      if (e == cudaSuccess) e = block_mul(n, (double2*)R0.p, n, m, (double2*)g.p, (double2*)d.R.p, n, mk, 1.0, 0.0, h->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+      if (e != cudaSuccess) {
+        cleanup();
+        return OV_ERR_CUDA;
+      }
+      if (herm) {
+        e = cudaMemcpyAsync(d.L.p, d.R.p, sizeof(double2) * n * mk, cudaMemcpyDeviceToDevice, h->st);
+      } else {
+        // L <- L (L^dag R)^{-dag} on the kept pairs, so that L^dag R = 1
+        std::fill(C.begin(), C.end(), make_double2(0.0, 0.0));
+        for (int c = 0; c < mk; ++c) C[(size_t)perm[keep[c]] * mk + c] = make_double2(1.0, 0.0);
+        std::vector<double2> M((size_t)mk * mk), Mi((size_t)mk * mk);
+        e = cudaMemcpyAsync(g.p, C.data(), sizeof(double2) * m * mk, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess)
+          e = block_mul(n, (double2*)L0.p, n, m, (double2*)g.p, (double2*)tmp.p, n, mk, 1.0, 0.0, h->st);
+        if (e == cudaSuccess)
+          e = block_gram(n, (double2*)tmp.p, n, mk, (double2*)d.R.p, n, mk, (double2*)part.p, (double2*)g.p, h->st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(M.data(), g.p, sizeof(double2) * mk * mk, cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess || !small_inv(mk, M.data(), Mi.data())) {
+          cleanup();
+          return e != cudaSuccess ? OV_ERR_CUDA : OV_ERR_BREAKDOWN;
+        }
+        std::vector<double2> Ci((size_t)mk * mk);
+        for (int i = 0; i < mk; ++i)
+          for (int j = 0; j < mk; ++j)
+            Ci[(size_t)i * mk + j] = make_double2(Mi[(size_t)j * mk + i].x, -Mi[(size_t)j * mk + i].y);  // Minv^dag
+        e = cudaMemcpyAsync(g.p, Ci.data(), sizeof(double2) * mk * mk, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess)
+          e = block_mul(n, (double2*)tmp.p, n, mk, (double2*)g.p, (double2*)d.L.p, n, mk, 1.0, 0.0, h->st);
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+      if (e != cudaSuccess) {
+        cleanup();
+        return OV_ERR_CUDA;
+      }
+    }
+    cleanup();
+    d.m = mk;
+    d.lam.clear();
+    d.res.clear();
+    for (int c = 0; c < mk; ++c) {
+      d.lam.push_back(lam[keep[c]]);
+      d.res.push_back(res[keep[c]]);
+    }
+    if (m_used) m_used[q] = mk;
+    for (int i = 0; i < m; ++i) {
+      if (lam_out) {
+        lam_out[2 * ((size_t)q * m + i)] = lam[i].real();
+        lam_out[2 * ((size_t)q * m + i) + 1] = lam[i].imag();
+      }
+      if (res_out) res_out[(size_t)q * m + i] = res[i];
+    }
+  }
+  return worst;
+}
+
+extern "C" int ov_get_deflation(const ov_handle* h, int lattice, int mcap, void* lam, void* R, void* L, int* m) {
+  if (!h || lattice < 0 || lattice >= (int)h->lat.size() || mcap < 0) return OV_ERR_ARG;
+  CK(cudaSetDevice(h->dev));
+  const int md = lattice < (int)h->defl.size() ? h->defl[lattice].m : 0;
+  const int mm = std::min(mcap, md);
+  if (m) *m = mm;
+  if (mm == 0) return OV_OK;
+  const auto& d = h->defl[lattice];
+  const size_t n = 12 * (size_t)h->lat[lattice].g.V;
+  if (lam)
+    for (int i = 0; i < mm; ++i) ((double2*)lam)[i] = make_double2(d.lam[i].real(), d.lam[i].imag());
+  if (R) CK(cudaMemcpy(R, d.R.p, sizeof(double2) * n * mm, cudaMemcpyDeviceToHost));
+  if (L) CK(cudaMemcpy(L, d.L.p, sizeof(double2) * n * mm, cudaMemcpyDeviceToHost));
+  return OV_OK;
+}
 int ov::handle_device(const ov_handle* h) { return h->dev; }
 size_t ov::handle_pool(const ov_handle* h, int nrhs) {
   if (h->is_batch) {

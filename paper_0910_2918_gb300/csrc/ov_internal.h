@@ -4,6 +4,9 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <complex>
+#include <vector>
+
 #include "../../include/ov.h"
 
 namespace ov {
@@ -185,6 +188,27 @@ int sign_apply_device(ov_handle* h, int nrhs, const double2* x, double2* y, doub
 cudaStream_t handle_stream(const ov_handle* h);
 int handle_device(const ov_handle* h);
 size_t handle_pool(const ov_handle* h, int nrhs);  // complex entries of nrhs vectors (0: not allowed)
+
+// block operations of the eigensolver and the deflated apply (ov_eig.cu); blocks are
+// bx (or by) canonical complex-double n-vectors with strides ldx (ldy)
+size_t lattice_size(const ov_handle* h, int q);  // 12 V of lattice q
+double lattice_mu(const ov_handle* h, int q);
+double lattice_mass(const ov_handle* h, int q);  // m_w + 4
+// Y = A X (dagger = 0) or A^dag X for b vectors of lattice q, in the handle's arithmetic
+int apply_block(ov_handle* h, int q, int b, const double2* X, double2* Y, int dagger);
+size_t block_gram_part_bytes(int bx, int by);
+cudaError_t block_gram(size_t n, const double2* X, size_t ldx, int bx, const double2* Y, size_t ldy, int by,
+                       double2* part, double2* G, cudaStream_t st);  // G = X^dag Y (bx x by, row-major)
+cudaError_t block_mul(size_t n, const double2* X, size_t ldx, int bx, const double2* C, double2* Y, size_t ldy, int by,
+                      double alpha, double beta, cudaStream_t st);  // Y = beta Y + alpha X C
+cudaError_t add_x_gamma5(size_t n, const double2* x, double2* y, cudaStream_t st);  // y = x + gamma5 y
+int eig_smallest(ov_handle* h, int q, int dagger, int m, int b, int deg, double tol, int maxit, double2* Rout,
+                 std::vector<std::complex<double>>& lam, std::vector<double>& res, int* iters, int verbose);
+// small dense complex matrices, row-major, on the host (ov_small.cpp)
+bool small_eig(int n, const double2* A, double2* w, double2* V);
+bool small_eigh(int n, const double2* A, double* w, double2* V);
+bool small_chol_inv(int n, const double2* A, double2* Rinv);
+bool small_inv(int n, const double2* A, double2* X);
 
 // learned sizing (ov_mlp.cu)
 cudaError_t mlp_predict_device(const float* theta_dev, int n, const float* X_dev, float* Y_dev, cudaStream_t st);
