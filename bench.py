@@ -45,6 +45,10 @@ TOL_MIXED, MIXED_STOP, MIXED_REPS = 1e-6, 5e-7, 3
 # the 48-lattice float batch: its Haar lattices converge slowly, where the estimate (the change
 # of c over 25 steps) undershoots the error by up to ~4x, so it stops 10x below its 1e-6 bar
 BATCH_FP32_STOP = 1e-7
+# deflation on the 48-lattice batch (Sec. 2): m eigenpairs per lattice; the strict and the
+# deflated double-float lines stop at DEFL_STOP, 10x below their 1e-8 bar (the same undershoot
+# of the estimate on the slowly converging lattices, with or without deflation)
+DEFL_M, DEFL_EIG_TOL, DEFL_MAXIT, DEFL_STOP = 16, 1e-9, 60, 1e-9
 L_MAX = 120
 NRHS = 12
 PREC = "df64"
@@ -702,8 +706,10 @@ def extra_configs(ov, torch):
     timed region), with their accuracy against the FP64 path:
     - the batch of 48 independent lattices of uneven size (12 each of 4^4, 6^4, 6^3x12,
       8^4; Haar or near-unit links; mu in [0, 0.5]; one Gaussian source each) in one
-      handle: float vectors (1e-6 bar) and double-float with learned sizing and relaxed
-      steps (1e-8 bar), against the FP64 path at 1e-10;
+      handle: float vectors (1e-6 bar), double-float with learned sizing and relaxed
+      steps (1e-8 bar), double-float with strict steps, and the same with the 16 critical
+      eigenpairs of every lattice deflated (Sec. 2; setup timed separately), against the FP64
+      path at 1e-10;
     - the learned-sizing evaluation lattice 24^3 x 48 (mu = 0.1, near-unit eps = 0.3,
       m_w = -1.6, one Gaussian source), double-float with relaxed steps, two-pass
       recombination, tol 1e-8 (stop at TOL_STOP), with and without the learned sizing."""
@@ -718,15 +724,27 @@ def extra_configs(ov, torch):
     mws, mus = [p["m_w"] for p in probs], [p["mu"] for p in probs]
     res = {}
     theta = sizer.load(sizer.DEFAULT_PARAMS)
+    defl = {}
     for form, prec, tol, ob in (("fp32", "fp32", BATCH_FP32_STOP, dict(check_interval=CHECK_EVERY,
                                                                         first_check=CHECK_FIRST)),
                                 ("fp64", "fp64", 1e-10, dict(check_interval=10)),
                                 ("df64", "df64", TOL_STOP, dict(check_interval=CHECK_EVERY, first_check=CHECK_FIRST,
-                                                                relax=RELAX))):
+                                                                relax=RELAX)),
+                                ("df64_strict", "df64", DEFL_STOP, dict(check_interval=CHECK_EVERY,
+                                                                        first_check=CHECK_FIRST)),
+                                ("df64_deflated", "df64", DEFL_STOP, dict(check_interval=CHECK_EVERY,
+                                                                          first_check=CHECK_FIRST))):
         hb = ov.ov_batch_create(dims, Us, mws, mus, prec, opts=ov.make_opts(**ob))
         try:
             if form == "df64":
                 ov.ov_set_sizer(hb, theta, 8, L_MAX)
+            if form == "df64_deflated":
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, lam, dres, used = ov.ov_deflate(hb, DEFL_M, tol=DEFL_EIG_TOL, maxit=DEFL_MAXIT, nlat=48)
+                torch.cuda.synchronize()
+                defl = {"setup_s": time.perf_counter() - t0, "pairs_used_mean": float(used.mean()),
+                        "pairs_used_min": int(used.min()), "m": DEFL_M, "eig_tol": DEFL_EIG_TOL}
             ys = [torch.zeros_like(x) for x in xs]
             ov.ov_batch_sign_apply(hb, xs, ys, tol, 1000, 100)
             torch.cuda.synchronize()
@@ -736,7 +754,7 @@ def extra_configs(ov, torch):
             res[form] = (ys, infos, time.perf_counter() - t0, ov.ov_get_stats(hb))
         finally:
             ov.ov_destroy(hb)
-    for form, bar in (("fp32", 1e-6), ("df64", TOL)):
+    for form, bar in (("fp32", 1e-6), ("df64", TOL), ("df64_strict", TOL), ("df64_deflated", TOL)):
         ys, infos, secs, st = res[form]
         ok = [i for i in range(48) if infos[i]["status"] == 0 and res["fp64"][1][i]["status"] == 0]
         errs = [float(torch.linalg.norm(ys[i] - res["fp64"][0][i]) / torch.linalg.norm(res["fp64"][0][i]))
@@ -744,12 +762,18 @@ def extra_configs(ov, torch):
         out["batch48_" + form] = {
             "problems_per_s": 48 / secs, "ms": secs * 1e3, "converged": len(ok), "bar": bar,
             "rel_err_vs_fp64_path_max": max(errs) if errs else None, "within_bar": sum(e <= bar for e in errs),
-            "stop_tol": BATCH_FP32_STOP if form == "fp32" else TOL_STOP,
+            "stop_tol": {"fp32": BATCH_FP32_STOP, "df64": TOL_STOP}.get(form, DEFL_STOP),
             "outer_steps": st["outer_steps"], "relaxed_steps": st["relaxed_steps"],
             "graph_launches": st["graph_launches"], "block_size": st["block_size"],
-            "form": ("float vectors and links" if form == "fp32" else
-                     "double-float, learned sizing, float hopping from %.1f x k* on" % RELAX)
+            "form": {"fp32": "float vectors and links",
+                     "df64": "double-float, learned sizing, float hopping from %.1f x k* on" % RELAX,
+                     "df64_strict": "double-float, strict steps, no sizing, no deflation",
+                     "df64_deflated": ("double-float, strict steps, no sizing, the %d eigenpairs of smallest |lambda| "
+                                       "per lattice deflated (Sec. 2; pairs with residual <= %g kept; setup not in ms)"
+                                       % (DEFL_M, DEFL_EIG_TOL))}[form]
             + "; one handle, one launch per outer step for all 48 lattices, CUDA graphs of 8 steps"}
+        if form == "df64_deflated":
+            out["batch48_" + form]["deflation"] = defl
     dims = (24, 24, 24, 48)
     U5 = oi.gauge_field(dims, "near_unit", 0, eps=0.3)
     x5 = oi.gaussian_source(dims, 1)

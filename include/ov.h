@@ -126,7 +126,10 @@ typedef struct {
                            Relaxation of the matvec accuracy in the late Krylov steps
                            (inexact Krylov methods: van den Eshof and Sleijpen, SIAM J. Matrix Anal.
                            Appl. 26 (2004)); not part of the paper's method. Both recombination
-                           modes switch at the same step [0] */
+                           modes switch at the same step. Ignored by a handle with deflation
+                           attached (ov_deflate): there the float hopping error brings back
+                           components along the removed eigenvectors, and measured on the
+                           48-lattice batch 13 of 48 lattices then stop converging [0] */
   int overlap_checks;   /* 1: a stopping check runs on a second, high-priority stream while up to
                            20 further outer steps (fewer than check_interval) run speculatively;
                            a run that stops at the check uses k = the check's step, so results

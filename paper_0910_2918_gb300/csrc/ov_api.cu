@@ -620,7 +620,7 @@ static int graph_for(ov_handle* h, const StepArgs& a, int prec, int mode, int U,
 
 // ---------------------------------------------------------------- sign apply
 static int sign_apply_core(ov_handle* h, int nrhs, const void* x, void* y, int mem, double tol, int k_max, int l,
-                           ov_info* info, int add_x, int neg_mu = 0) {
+                           ov_info* info, int add_x, int neg_mu = 0, int strict_only = 0) {
   const Phase ph_apply("ov_sign_apply");
   if (!h || !x || !y || nrhs < 1 || k_max < 1 || l < 1 || !(tol >= 0.0)) return OV_ERR_ARG;
   if (mem != OV_MEM_HOST && mem != OV_MEM_DEVICE) return OV_ERR_ARG;
@@ -742,8 +742,11 @@ static int sign_apply_core(ov_handle* h, int nrhs, const void* x, void* y, int m
   a.slot_tab = recomb == OV_RECOMB_STORED ? (void* const*)h->slot_tab.p : nullptr;
   const int gU = (o.timing || o.graph_steps <= 0) ? 0 : o.graph_steps;
   // relaxed steps (double-float handles): float hopping from step relax_from on, the
-  // same step in both passes
-  const bool relaxing = o.relax > 0.0 && h->prec == OV_PREC_DF64;
+  // same step in both passes; never on a deflated source (strict_only): the float
+  // hopping error, ~1e-7 of |A v| in every direction, puts back components along the
+  // removed eigenvectors, whose eigenvalues lie inside the deflation gap that the
+  // shortened Krylov space no longer resolves
+  const bool relaxing = !strict_only && o.relax > 0.0 && h->prec == OV_PREC_DF64;
   int relax_from = INT_MAX;
   if (relaxing) {
     if (o.k_fixed > 0) relax_from = std::max(1, (int)std::ceil(o.relax * o.k_fixed));
@@ -1247,7 +1250,7 @@ static int sign_apply_impl(ov_handle* h, int nrhs, const void* x, void* y, int m
   }
   CK(cudaStreamSynchronize(st));
   // the Krylov part on the deflated source, in place in dy (its result overwrites it)
-  int rc = sign_apply_core(h, nrhs, h->dy.p, h->dx.p, OV_MEM_DEVICE, tol, k_max, l, info, 0, neg_mu);
+  int rc = sign_apply_core(h, nrhs, h->dy.p, h->dx.p, OV_MEM_DEVICE, tol, k_max, l, info, 0, neg_mu, 1);
   if (rc < 0) return rc;
   // y = y' + R sgn(Lambda) c  (and x + gamma5 (...) for the overlap operator)
   for (size_t g = 0; g < grps.size(); ++g) {
@@ -1291,26 +1294,94 @@ size_t ov::lattice_size(const ov_handle* h, int q) { return 12 * (size_t)h->lat[
 double ov::lattice_mu(const ov_handle* h, int q) { return h->lat[q].mu; }
 double ov::lattice_mass(const ov_handle* h, int q) { return h->lat[q].m_w + 4.0; }
 
-int ov::apply_block(ov_handle* h, int q, int b, const double2* X, double2* Y, int dagger) {
-  cudaStream_t st = h->st;
-  const std::vector<int> lat_of(b, q);
-  Batch bt;
+// A fixed set of matvecs (one per item: lattice, sign of mu, offset of the vector in the
+// canonical block buffers), its problem descriptors and block map uploaded once; every run
+// is one pack, one stencil launch and one unpack over all items.
+struct ov::ApplySet {
+  Buf desc, map;
+  Batch bt{};
   size_t pool = 0;
-  int rc = build_batch(h, lat_of, h->o.block_size ? h->o.block_size : kBlockDefault, &bt, &pool);
-  if (rc != OV_OK) return rc;
-  rc = ensure_outer(h, b, std::max(h->cap_ld, 4), pool, max_blocks(h, lat_of));
+  int nitems = 0, maxblk = 0;
+};
+
+int ov::apply_set_create(ov_handle* h, const std::vector<ApplyItem>& items, size_t pool, ApplySet** out) {
+  *out = nullptr;
+  if (items.empty()) return OV_ERR_ARG;
+  const int bs = h->o.block_size ? h->o.block_size : kBlockDefault;
+  const int np = (int)items.size();
+  std::vector<ProbDesc> d(np);
+  std::vector<int2> map;
+  int blk = 0, maxblk = 0;
+  bool same = true;
+  for (int r = 0; r < np; ++r) {
+    const ApplyItem& it = items[r];
+    if (it.q < 0 || it.q >= (int)h->lat.size() || it.voff + 12 * (size_t)h->lat[it.q].g.V > pool) return OV_ERR_ARG;
+    const Lattice& L = h->lat[it.q];
+    d[r].g = L.g;
+    d[r].links = L.links.p;
+    fill_consts(d[r], L.m_w, it.neg ? -L.mu : L.mu);
+    d[r].voff = it.voff;
+    d[r].block0 = blk;
+    d[r].nblk = num_site_blocks(L.g, bs);
+    blk += d[r].nblk;
+    maxblk += num_site_blocks(L.g, 64);
+    same = same && it.q == items[0].q;
+  }
+  // as build_batch: site-block-major for one lattice (the items share links in L2)
+  if (same) {
+    for (int qb = 0; qb < d[0].nblk; ++qb)
+      for (int r = 0; r < np; ++r) map.push_back(make_int2(r, qb));
+  } else {
+    for (int r = 0; r < np; ++r)
+      for (int qb = 0; qb < d[r].nblk; ++qb) map.push_back(make_int2(r, qb));
+  }
+  ApplySet* a = new ApplySet;
+  if (grow(a->desc, sizeof(ProbDesc) * np) != cudaSuccess || grow(a->map, sizeof(int2) * map.size()) != cudaSuccess) {
+    apply_set_destroy(a);
+    return OV_ERR_NOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(a->desc.p, d.data(), sizeof(ProbDesc) * np, cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(a->map.p, map.data(), sizeof(int2) * map.size(), cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);  // the host vectors go out of scope
+  if (e != cudaSuccess) {
+    apply_set_destroy(a);
+    return OV_ERR_CUDA;
+  }
+  a->bt.desc = (const ProbDesc*)a->desc.p;
+  a->bt.blk_map = (const int2*)a->map.p;
+  a->bt.nblocks = blk;
+  a->bt.nprob = np;
+  a->bt.block = bs;
+  a->pool = pool;
+  a->nitems = np;
+  a->maxblk = maxblk;
+  *out = a;
+  return OV_OK;
+}
+
+void ov::apply_set_destroy(ApplySet* a) {
+  if (!a) return;
+  release(a->desc);
+  release(a->map);
+  delete a;
+}
+
+int ov::apply_set_run(ov_handle* h, const ApplySet* a, const double2* X, double2* Y) {
+  cudaStream_t st = h->st;
+  int rc = ensure_outer(h, std::max(a->nitems, h->cap_rhs), std::max(h->cap_ld, 4), a->pool, a->maxblk);
   if (rc != OV_OK) return rc;
   Coefs c = coefs(h, h->cap_ld);
-  CK(launch_pack(h->prec, bt, X, h->tv.p, nullptr, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, nullptr,
+  CK(launch_pack(h->prec, a->bt, X, h->tv.p, nullptr, c, (double*)h->partials.p, (unsigned*)h->counters.p, 0, nullptr,
                  st));
-  StepArgs a{};
-  a.b = bt;
-  a.tv = h->tv.p;
-  a.p = h->p.p;
-  a.dagger = dagger ? 1 : 0;
-  a.c = c;
-  CK(launch_step(h->prec, kModeApply, a, st));
-  CK(launch_unpack(h->prec, bt, h->p.p, Y, st));
+  StepArgs sa{};
+  sa.b = a->bt;
+  sa.tv = h->tv.p;
+  sa.p = h->p.p;
+  sa.dagger = 0;
+  sa.c = c;
+  CK(launch_step(h->prec, kModeApply, sa, st));
+  CK(launch_unpack(h->prec, a->bt, h->p.p, Y, st));
   h->stats.launches += 3;
   h->stats.stencil_launches += 1;
   h->stats.other_launches += 2;
@@ -1321,51 +1392,87 @@ extern "C" int ov_deflate(ov_handle* h, int m, double tol, int maxit, double* la
   if (!h || m < 0 || !(tol > 0.0) || maxit < 1) return OV_ERR_ARG;
   if (m > 48) return OV_ERR_TOO_LARGE;
   CK(cudaSetDevice(h->dev));
+  const Phase ph("ov_deflate");
   const int nl = (int)h->lat.size();
+  for (int q = 0; q < nl; ++q)
+    if ((size_t)2 * m + 8 > 12 * (size_t)h->lat[q].g.V && m > 0) return OV_ERR_ARG;
   h->defl.resize(nl);
-  int worst = OV_OK;
   for (int q = 0; q < nl; ++q) {
-    auto& d = h->defl[q];
-    d.m = 0;
+    h->defl[q].m = 0;
     if (m_used) m_used[q] = 0;
-    if (m == 0) {
+  }
+  if (m == 0) {
+    for (auto& d : h->defl) {
       release(d.R);
       release(d.L);
-      continue;
     }
+    return OV_OK;
+  }
+  // a block of 2 m + 8 vectors: the filter's gap is between the m-th and the b-th eigenvalue
+  const int b = std::min<int>(64, 2 * m + 8);
+  const int deg = 48;  // the filter's largest degree (ov_eig.cu lowers it while the cut is high)
+  // one job per lattice for the right eigenvectors, one more at mu != 0 for the left ones
+  // (right eigenvectors of A^dag = A(-mu) for conj(lambda)); all jobs run together
+  std::vector<Buf> R0(nl), L0(nl);
+  std::vector<EigJob> jobs;
+  std::vector<int> jr(nl, -1), jl(nl, -1);
+  size_t nmax = 0;
+  Buf tmp, part, g;
+  auto cleanup = [&]() {
+    for (int q = 0; q < nl; ++q) {
+      release(R0[q]);
+      release(L0[q]);
+    }
+    release(tmp);
+    release(part);
+    release(g);
+  };
+  for (int q = 0; q < nl; ++q) {
     const size_t n = 12 * (size_t)h->lat[q].g.V;
-    if ((size_t)2 * m + 8 > n) return OV_ERR_ARG;
-    // a block of 2 m + 8 vectors: the filter's gap is between the m-th and the b-th eigenvalue
-    const int b = std::min<int>(64, 2 * m + 8);
-    const int deg = 16;
-    const bool herm = h->lat[q].mu == 0.0;
-    Buf R0, L0, tmp, part, g;
-    auto cleanup = [&]() {
-      for (Buf* bb : {&R0, &L0, &tmp, &part, &g}) release(*bb);
-    };
-    if (grow(R0, sizeof(double2) * n * m) != cudaSuccess || (!herm && grow(L0, sizeof(double2) * n * m) != cudaSuccess) ||
-        grow(tmp, sizeof(double2) * n * m) != cudaSuccess || grow(part, block_gram_part_bytes(m, m)) != cudaSuccess ||
-        grow(g, sizeof(double2) * m * m) != cudaSuccess) {
+    nmax = std::max(nmax, n);
+    if (grow(R0[q], sizeof(double2) * n * m) != cudaSuccess) {
       cleanup();
       return OV_ERR_NOMEM;
     }
-    std::vector<std::complex<double>> lam, lamL;
-    std::vector<double> res, resL;
-    int its = 0;
-    int rc = eig_smallest(h, q, 0, m, b, deg, tol, maxit, (double2*)R0.p, lam, res, &its, h->trace);
-    if (rc < 0) {
-      cleanup();
-      return rc;
+    EigJob jb;
+    jb.q = q;
+    jb.Rout = (double2*)R0[q].p;
+    jr[q] = (int)jobs.size();
+    jobs.push_back(jb);
+    if (h->lat[q].mu != 0.0) {
+      if (grow(L0[q], sizeof(double2) * n * m) != cudaSuccess) {
+        cleanup();
+        return OV_ERR_NOMEM;
+      }
+      jb.neg = 1;
+      jb.Rout = (double2*)L0[q].p;
+      jl[q] = (int)jobs.size();
+      jobs.push_back(jb);
     }
+  }
+  if (grow(tmp, sizeof(double2) * nmax * m) != cudaSuccess || grow(part, block_gram_part_bytes(m, m)) != cudaSuccess ||
+      grow(g, sizeof(double2) * m * m) != cudaSuccess) {
+    cleanup();
+    return OV_ERR_NOMEM;
+  }
+  const int erc = eig_smallest(h, jobs, m, b, deg, tol, maxit, h->trace);
+  if (erc < 0) {
+    cleanup();
+    return erc;
+  }
+  int worst = OV_OK;
+  for (int q = 0; q < nl; ++q) {
+    auto& d = h->defl[q];
+    const size_t n = 12 * (size_t)h->lat[q].g.V;
+    const bool herm = jl[q] < 0;
+    std::vector<std::complex<double>> lam = jobs[jr[q]].lam;
+    std::vector<double> res = jobs[jr[q]].res;
     std::vector<int> perm(m);
     for (int i = 0; i < m; ++i) perm[i] = i;
     if (!herm) {
-      // left eigenvectors: right eigenvectors of A^dag for conj(lambda), matched by eigenvalue
-      int rc2 = eig_smallest(h, q, 1, m, b, deg, tol, maxit, (double2*)L0.p, lamL, resL, &its, h->trace);
-      if (rc2 < 0) {
-        cleanup();
-        return rc2;
-      }
+      // left eigenvectors matched to the right ones by eigenvalue
+      const auto& lamL = jobs[jl[q]].lam;
+      const auto& resL = jobs[jl[q]].res;
       std::vector<int> used(m, 0);
       for (int i = 0; i < m; ++i) {
         int best = 0;
@@ -1387,13 +1494,17 @@ extern "C" int ov_deflate(ov_handle* h, int m, double tol, int maxit, double* la
       if (res[i] <= tol) keep.push_back(i);
     const int mk = (int)keep.size();
     if (mk < m) worst = OV_NOT_CONVERGED;
-    CK(grow(d.R, sizeof(double2) * n * std::max(mk, 1)));
-    CK(grow(d.L, sizeof(double2) * n * std::max(mk, 1)));
+    if (grow(d.R, sizeof(double2) * n * std::max(mk, 1)) != cudaSuccess ||
+        grow(d.L, sizeof(double2) * n * std::max(mk, 1)) != cudaSuccess) {
+      cleanup();
+      return OV_ERR_NOMEM;
+    }
     if (mk > 0) {
       std::vector<double2> C((size_t)m * mk, make_double2(0.0, 0.0));
       for (int c = 0; c < mk; ++c) C[(size_t)keep[c] * mk + c] = make_double2(1.0, 0.0);
       cudaError_t e = cudaMemcpyAsync(g.p, C.data(), sizeof(double2) * m * mk, cudaMemcpyHostToDevice, h->st);
-      if (e == cudaSuccess) e = block_mul(n, (double2*)R0.p, n, m, (double2*)g.p, (double2*)d.R.p, n, mk, 1.0, 0.0, h->st);
+      if (e == cudaSuccess)
+        e = block_mul(n, (double2*)R0[q].p, n, m, (double2*)g.p, (double2*)d.R.p, n, mk, 1.0, 0.0, h->st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
       if (e != cudaSuccess) {
         cleanup();
@@ -1408,7 +1519,7 @@ extern "C" int ov_deflate(ov_handle* h, int m, double tol, int maxit, double* la
         std::vector<double2> M((size_t)mk * mk), Mi((size_t)mk * mk);
         e = cudaMemcpyAsync(g.p, C.data(), sizeof(double2) * m * mk, cudaMemcpyHostToDevice, h->st);
         if (e == cudaSuccess)
-          e = block_mul(n, (double2*)L0.p, n, m, (double2*)g.p, (double2*)tmp.p, n, mk, 1.0, 0.0, h->st);
+          e = block_mul(n, (double2*)L0[q].p, n, m, (double2*)g.p, (double2*)tmp.p, n, mk, 1.0, 0.0, h->st);
         if (e == cudaSuccess)
           e = block_gram(n, (double2*)tmp.p, n, mk, (double2*)d.R.p, n, mk, (double2*)part.p, (double2*)g.p, h->st);
         if (e == cudaSuccess)
@@ -1432,7 +1543,6 @@ extern "C" int ov_deflate(ov_handle* h, int m, double tol, int maxit, double* la
         return OV_ERR_CUDA;
       }
     }
-    cleanup();
     d.m = mk;
     d.lam.clear();
     d.res.clear();
@@ -1449,6 +1559,7 @@ extern "C" int ov_deflate(ov_handle* h, int m, double tol, int maxit, double* la
       if (res_out) res_out[(size_t)q * m + i] = res[i];
     }
   }
+  cleanup();
   return worst;
 }
 

@@ -194,21 +194,40 @@ size_t handle_pool(const ov_handle* h, int nrhs);  // complex entries of nrhs ve
 size_t lattice_size(const ov_handle* h, int q);  // 12 V of lattice q
 double lattice_mu(const ov_handle* h, int q);
 double lattice_mass(const ov_handle* h, int q);  // m_w + 4
-// Y = A X (dagger = 0) or A^dag X for b vectors of lattice q, in the handle's arithmetic
-int apply_block(ov_handle* h, int q, int b, const double2* X, double2* Y, int dagger);
+// Fixed sets of matvecs in the handle's arithmetic: item r computes Y[voff..] = A X[voff..]
+// for 12 V entries of lattice q at mu (neg = 0) or at -mu (neg = 1: A(-mu) = A^dag); X and Y
+// are canonical complex-double buffers of `pool` entries. One run = three launches.
+struct ApplyItem {
+  int q, neg;
+  size_t voff;
+};
+struct ApplySet;
+int apply_set_create(ov_handle* h, const std::vector<ApplyItem>& items, size_t pool, ApplySet** out);
+int apply_set_run(ov_handle* h, const ApplySet* s, const double2* X, double2* Y);
+void apply_set_destroy(ApplySet* s);
 size_t block_gram_part_bytes(int bx, int by);
 cudaError_t block_gram(size_t n, const double2* X, size_t ldx, int bx, const double2* Y, size_t ldy, int by,
                        double2* part, double2* G, cudaStream_t st);  // G = X^dag Y (bx x by, row-major)
 cudaError_t block_mul(size_t n, const double2* X, size_t ldx, int bx, const double2* C, double2* Y, size_t ldy, int by,
                       double alpha, double beta, cudaStream_t st);  // Y = beta Y + alpha X C
 cudaError_t add_x_gamma5(size_t n, const double2* x, double2* y, cudaStream_t st);  // y = x + gamma5 y
-int eig_smallest(ov_handle* h, int q, int dagger, int m, int b, int deg, double tol, int maxit, double2* Rout,
-                 std::vector<std::complex<double>>& lam, std::vector<double>& res, int* iters, int verbose);
+// the m eigenpairs of smallest |lambda| of A(+-mu) on each job's lattice, all jobs in the
+// same launches (ov_eig.cu)
+struct EigJob {
+  int q = 0, neg = 0;  // lattice; 1: eigenvectors of A(-mu) = A^dag
+  double2* Rout = nullptr;  // [m][n] device: right eigenvectors (unit norm)
+  std::vector<std::complex<double>> lam;  // eigenvalues, by increasing magnitude
+  std::vector<double> res;                // ||A x - lambda x|| / ||A|| per pair
+  int its = 0;
+  int status = 0;  // OV_OK, OV_NOT_CONVERGED (best vectors returned) or OV_ERR_BREAKDOWN
+};
+int eig_smallest(ov_handle* h, std::vector<EigJob>& jobs, int m, int b, int deg, double tol, int maxit, int verbose);
 // small dense complex matrices, row-major, on the host (ov_small.cpp)
 bool small_eig(int n, const double2* A, double2* w, double2* V);
 bool small_eigh(int n, const double2* A, double* w, double2* V);
 bool small_chol_inv(int n, const double2* A, double2* Rinv);
 bool small_inv(int n, const double2* A, double2* X);
+bool small_qr_q(int n, const double2* A, double2* Q);  // unitary Q of A = Q R
 
 // learned sizing (ov_mlp.cu)
 cudaError_t mlp_predict_device(const float* theta_dev, int n, const float* X_dev, float* Y_dev, cudaStream_t st);

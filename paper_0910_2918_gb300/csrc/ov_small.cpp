@@ -6,7 +6,9 @@
 // problem. Methods: cyclic Jacobi for Hermitian matrices (Golub and Van Loan, Matrix
 // Computations, 4th ed., Sec. 8.5), Householder reduction to Hessenberg form and the
 // shifted QR iteration for general complex matrices (ibid., Secs. 7.4-7.5), eigenvectors
-// of the triangular Schur factor by back substitution (ibid., Sec. 7.6.4).
+// of the triangular Schur factor by back substitution (ibid., Sec. 7.6.4), and the unitary
+// factor of a QR factorisation by modified Gram-Schmidt applied twice (ibid., Sec. 5.2.8;
+// Giraud, Langou and Rozloznik, Comput. Math. Appl. 50 (2005) for the second pass).
 #include <math.h>
 
 #include <algorithm>
@@ -286,6 +288,52 @@ bool small_inv(int n, const double2* A_in, double2* X_out) {
     }
   }
   for (size_t e = 0; e < (size_t)n * n; ++e) X_out[e] = make_double2(X[e].real(), X[e].imag());
+  return true;
+}
+
+// Q (row-major n x n, unitary) with A = Q R, R upper triangular: the leading j columns of Q
+// span those of A for every j. A column that is numerically dependent on the ones before it
+// is replaced by the unit vector that keeps the most after projection (Q stays unitary).
+bool small_qr_q(int n, const double2* A_in, double2* Q_out) {
+  std::vector<cd> Q((size_t)n * n);
+  for (size_t i = 0; i < (size_t)n * n; ++i) Q[i] = cd(A_in[i].x, A_in[i].y);
+  auto q = [&](int i, int j) -> cd& { return Q[(size_t)i * n + j]; };
+  std::vector<cd> u(n);
+  auto project = [&](int j) {  // column j minus its components along columns 0 .. j-1
+    for (int k = 0; k < j; ++k) {
+      cd d = 0.0;
+      for (int i = 0; i < n; ++i) d += std::conj(q(i, k)) * q(i, j);
+      for (int i = 0; i < n; ++i) q(i, j) -= d * q(i, k);
+    }
+  };
+  auto norm = [&](int j) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += std::norm(q(i, j));
+    return sqrt(s);
+  };
+  for (int j = 0; j < n; ++j) {
+    const double n0 = norm(j);
+    project(j);
+    project(j);
+    double nj = norm(j);
+    if (!(nj > 1e-10 * n0) || !(nj > 0.0)) {
+      int best = -1;
+      double keep = -1.0;
+      for (int e = 0; e < n; ++e) {
+        for (int i = 0; i < n; ++i) q(i, j) = i == e ? 1.0 : 0.0;
+        project(j);
+        const double r = norm(j);
+        if (r > keep) { keep = r; best = e; }
+      }
+      for (int i = 0; i < n; ++i) q(i, j) = i == best ? 1.0 : 0.0;
+      project(j);
+      project(j);
+      nj = norm(j);
+      if (!(nj > 0.5 / sqrt((double)n))) return false;  // some unit vector keeps >= 1/sqrt(n)
+    }
+    for (int i = 0; i < n; ++i) q(i, j) /= nj;
+  }
+  for (size_t i = 0; i < (size_t)n * n; ++i) Q_out[i] = make_double2(Q[i].real(), Q[i].imag());
   return true;
 }
 

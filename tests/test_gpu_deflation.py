@@ -110,3 +110,52 @@ def test_deflated_solver_adjoint(ov):
         rc, its, res = op.solve(b, x, mass=mass, tol=1e-9, maxit=300, sign_tol=1e-11, k_max=384, l=120)
     assert rc == 0
     assert rel(x[0], np.linalg.solve(D, b[0])) < 1e-7
+
+
+def test_batch_deflation_per_lattice(ov):
+    """A batch handle deflates every lattice in the same launches (one eigensolver job per
+    lattice and side): each lattice's eigenvalues are those of full diagonalisation, and the
+    deflated batch apply equals the deflated single-lattice applies."""
+    probs = [((4, 4, 4, 4), "haar", 0, -1.5, 0.0), ((2, 2, 2, 4), "haar", 0, -1.5, 0.3),
+             ((2, 4, 2, 4), "haar", 5, -1.4, 0.2)]
+    m, k = 8, 60
+    Us = [oi.gauge_field(d, kind, seed) for d, kind, seed, _, _ in probs]
+    xs = [oi.gaussian_source(d, 11 + i).reshape(1, -1).copy() for i, (d, _, _, _, _) in enumerate(probs)]
+    hb = ov.ov_batch_create([p[0] for p in probs], Us, [p[3] for p in probs], [p[4] for p in probs], "fp64",
+                            opts=ov.make_opts(k_fixed=k))
+    try:
+        rc, lam, res, used = ov.ov_deflate(hb, m, tol=1e-11, maxit=300, nlat=len(probs))
+        ys = [np.zeros_like(x) for x in xs]
+        ov.ov_batch_sign_apply(hb, xs, ys, 0.0, k, 50)
+    finally:
+        ov.ov_destroy(hb)
+    assert rc == 0 and list(used) == [m] * len(probs)
+    for i, (d, kind, seed, m_w, mu) in enumerate(probs):
+        ev = np.linalg.eigvals(dirac.dense_A(Us[i], d, m_w, mu))
+        ev = ev[np.argsort(np.abs(ev))[:m]]
+        for z in lam[i]:
+            assert np.abs(ev - z).min() < 1e-9
+        y1 = np.zeros_like(xs[i])
+        with ov.Overlap(d, Us[i], m_w, mu, "fp64", opts=ov.make_opts(k_fixed=k)) as op:
+            op.deflate(m, tol=1e-11, maxit=300)
+            op.sign_apply(xs[i], y1, 0.0, k, 50)
+        assert rel(ys[i][0], y1[0]) < 1e-10, (i, rel(ys[i][0], y1[0]))
+
+
+def test_deflated_handle_runs_strict_steps(ov):
+    """With deflation attached a double-float handle ignores opts.relax: its float hopping
+    error would put back components along the removed eigenvectors. The deflated apply with
+    relax set is bitwise the one without, and counts no relaxed step."""
+    dims, mu, k = (4, 4, 4, 4), 0.3, 160
+    U = oi.gauge_field(dims, "haar", 0)
+    x = oi.gaussian_source(dims, 2).reshape(1, -1).copy()
+    out = []
+    for relax in (0.0, 0.5):
+        y = np.zeros_like(x)
+        with ov.Overlap(dims, U, -1.5, mu, "df64", opts=ov.make_opts(k_fixed=k, relax=relax)) as op:
+            op.deflate(8, tol=1e-10, maxit=300)
+            op.reset_stats()
+            op.sign_apply(x, y, 0.0, k, 100)
+            out.append((y, op.stats()["relaxed_steps"]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == 0 and out[1][1] == 0

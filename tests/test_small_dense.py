@@ -1,6 +1,7 @@
 """The host routines of the eigensolver's Rayleigh-Ritz step (csrc/ov_small.cpp) against
 their definitions: A V = V diag(w) with unit columns (general and Hermitian matrices,
-including repeated eigenvalues), R^dag R = A with Rinv R = 1, and A A^-1 = 1. The file is
+including repeated eigenvalues), R^dag R = A with Rinv R = 1, A A^-1 = 1, and A = Q R with Q
+unitary and R upper triangular. The file is
 compiled alone with the host compiler for this test (no GPU needed)."""
 import ctypes
 import os
@@ -17,11 +18,13 @@ bool small_eig(int n, const double2* A, double2* w, double2* V);
 bool small_eigh(int n, const double2* A, double* w, double2* V);
 bool small_chol_inv(int n, const double2* A, double2* Rinv);
 bool small_inv(int n, const double2* A, double2* X);
+bool small_qr_q(int n, const double2* A, double2* Q);
 }
 extern "C" int t_eig(int n, const double2* A, double2* w, double2* V) { return ov::small_eig(n, A, w, V); }
 extern "C" int t_eigh(int n, const double2* A, double* w, double2* V) { return ov::small_eigh(n, A, w, V); }
 extern "C" int t_chol(int n, const double2* A, double2* R) { return ov::small_chol_inv(n, A, R); }
 extern "C" int t_inv(int n, const double2* A, double2* X) { return ov::small_inv(n, A, X); }
+extern "C" int t_qr(int n, const double2* A, double2* Q) { return ov::small_qr_q(n, A, Q); }
 '''
 
 
@@ -107,3 +110,31 @@ def test_cholesky_inverse_and_inverse(lib):
     # not positive definite: refused
     A2 = np.ascontiguousarray(-A)
     assert lib.t_chol(n, c128p(A2), c128p(Ri)) == 0
+
+
+@pytest.mark.parametrize("n", [1, 5, 40, 64])
+def test_qr_unitary_factor(lib, n):
+    rng = np.random.default_rng(100 + n)
+    A = np.ascontiguousarray(rand_c(rng, n))
+    Q = np.zeros((n, n), complex)
+    assert lib.t_qr(n, c128p(A), c128p(Q)) == 1
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(n)) < 1e-13 * n
+    R = Q.conj().T @ A
+    assert np.linalg.norm(np.tril(R, -1)) < 1e-12 * np.linalg.norm(A)  # leading spans kept
+
+
+def test_qr_dependent_columns(lib):
+    # columns 1 and 3 repeat column 0: Q stays unitary and column 0's direction leads
+    rng = np.random.default_rng(7)
+    n = 6
+    A = rand_c(rng, n)
+    A[:, 1] = A[:, 0]
+    A[:, 3] = 2j * A[:, 0]
+    A = np.ascontiguousarray(A)
+    Q = np.zeros((n, n), complex)
+    assert lib.t_qr(n, c128p(A), c128p(Q)) == 1
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(n)) < 1e-12
+    q0 = A[:, 0] / np.linalg.norm(A[:, 0])
+    assert abs(abs(np.vdot(Q[:, 0], q0)) - 1.0) < 1e-12
+    R = Q.conj().T @ A
+    assert np.linalg.norm(np.tril(R, -1)) < 1e-11 * np.linalg.norm(A)
