@@ -724,16 +724,17 @@ def extra_configs(ov, torch):
     mws, mus = [p["m_w"] for p in probs], [p["mu"] for p in probs]
     res = {}
     theta = sizer.load(sizer.DEFAULT_PARAMS)
-    defl = {}
-    for form, prec, tol, ob in (("fp32", "fp32", BATCH_FP32_STOP, dict(check_interval=CHECK_EVERY,
-                                                                        first_check=CHECK_FIRST)),
+    defl, sched = {}, {}
+    # the float, strict and deflated lines place their checks adaptively (check_schedule = 1):
+    # a check of the 48 lattices costs ~20 ms, ~90 of the batch's outer steps, and the batch
+    # runs until its slowest lattice stops, so the checks jump towards the largest predicted k*
+    adaptive = dict(check_interval=CHECK_EVERY, first_check=CHECK_FIRST, check_schedule=1)
+    for form, prec, tol, ob in (("fp32", "fp32", BATCH_FP32_STOP, adaptive),
                                 ("fp64", "fp64", 1e-10, dict(check_interval=10)),
                                 ("df64", "df64", TOL_STOP, dict(check_interval=CHECK_EVERY, first_check=CHECK_FIRST,
                                                                 relax=RELAX)),
-                                ("df64_strict", "df64", DEFL_STOP, dict(check_interval=CHECK_EVERY,
-                                                                        first_check=CHECK_FIRST)),
-                                ("df64_deflated", "df64", DEFL_STOP, dict(check_interval=CHECK_EVERY,
-                                                                          first_check=CHECK_FIRST))):
+                                ("df64_strict", "df64", DEFL_STOP, adaptive),
+                                ("df64_deflated", "df64", DEFL_STOP, adaptive)):
         hb = ov.ov_batch_create(dims, Us, mws, mus, prec, opts=ov.make_opts(**ob))
         try:
             if form == "df64":
@@ -752,6 +753,7 @@ def extra_configs(ov, torch):
             rc, infos = ov.ov_batch_sign_apply(hb, xs, ys, tol, 1000, 100)
             torch.cuda.synchronize()
             res[form] = (ys, infos, time.perf_counter() - t0, ov.ov_get_stats(hb))
+            sched[form] = "adaptive" if ob.get("check_schedule") else "every %d" % ob["check_interval"]
         finally:
             ov.ov_destroy(hb)
     for form, bar in (("fp32", 1e-6), ("df64", TOL), ("df64_strict", TOL), ("df64_deflated", TOL)):
@@ -765,6 +767,7 @@ def extra_configs(ov, torch):
             "stop_tol": {"fp32": BATCH_FP32_STOP, "df64": TOL_STOP}.get(form, DEFL_STOP),
             "outer_steps": st["outer_steps"], "relaxed_steps": st["relaxed_steps"],
             "graph_launches": st["graph_launches"], "block_size": st["block_size"],
+            "checks": st["checks"], "check_schedule": sched[form],
             "form": {"fp32": "float vectors and links",
                      "df64": "double-float, learned sizing, float hopping from %.1f x k* on" % RELAX,
                      "df64_strict": "double-float, strict steps, no sizing, no deflation",

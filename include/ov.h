@@ -140,6 +140,12 @@ typedef struct {
                            stopping check takes c = sgn(H_k) e_1 by Roberts-Higham on the full
                            k x k Ritz matrix (FP64 Gauss-Jordan inversions over global memory,
                            k <= 1024; the inner estimate is 0), for comparing the two [1] */
+  int rh_scaling;       /* inner level in OV_INNER_DF64 arithmetic: 1 scales the Roberts-Higham steps
+                           by g = |det S_n|^{-1/l} while the iterate changes by more than 1e-2
+                           (Kenney and Laub, SIAM J. Matrix Anal. Appl. 13 (1992)), then takes the
+                           plain steps of Eq. (Roberts); the limit sgn(T_l) is the same, reached
+                           in fewer inversions. 0: the plain iteration throughout. The FP64 inner
+                           arithmetic and ov_rh_sign always take the plain iteration [1] */
 } ov_opts;
 
 #define OV_INNER_DF64 0

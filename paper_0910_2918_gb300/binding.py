@@ -48,7 +48,8 @@ class ov_opts(ctypes.Structure):
                 ("breakdown_tol", ctypes.c_double), ("inner_dl", ctypes.c_int), ("k_fixed", ctypes.c_int),
                 ("check_schedule", ctypes.c_int), ("block_size", ctypes.c_int), ("graph_steps", ctypes.c_int),
                 ("timing", ctypes.c_int), ("inner_arith", ctypes.c_int), ("relax", ctypes.c_double),
-                ("overlap_checks", ctypes.c_int), ("nested", ctypes.c_int)]
+                ("overlap_checks", ctypes.c_int), ("nested", ctypes.c_int),
+                ("rh_scaling", ctypes.c_int)]
 
 
 class ov_stats(ctypes.Structure):

@@ -225,6 +225,33 @@ extern "C" int ov_reset_stats(ov_handle* h) {
 // Problem descriptors of one call: problem r uses lattice lat_of[r]; vectors are pooled
 // (12 V_r complex entries per problem, in problem order). Uploads the descriptors and the
 // block map and returns the batch description and the pool size in complex entries.
+// Site blocks in an order that keeps the neighbour planes of a block recently touched: the
+// blocks are bs consecutive sites (x fastest), so the +-x (and mostly +-y) hops stay inside a
+// block and the +-z, +-t hops reach other blocks; sorting the blocks by the Morton code of
+// the (y, z, t) coordinates of their first site brings those blocks close in launch order,
+// so their vectors are still in L2 when the neighbours read them. The reductions index their
+// partial sums by the site block, so the order changes no result.
+static std::vector<int> block_order(const Geometry& g, int bs) {
+  const int nb = num_site_blocks(g, bs);
+  std::vector<std::pair<unsigned long long, int>> key(nb);
+  for (int q = 0; q < nb; ++q) {
+    const long long s = (long long)q * bs;
+    const unsigned y = (unsigned)((s / g.Lx) % g.Ly), z = (unsigned)((s / ((long long)g.Lx * g.Ly)) % g.Lz),
+                   t = (unsigned)(s / ((long long)g.Lx * g.Ly * g.Lz));
+    unsigned long long m = 0;
+    for (int bit = 0; bit < 16; ++bit) {
+      m |= (unsigned long long)((y >> bit) & 1u) << (3 * bit);
+      m |= (unsigned long long)((z >> bit) & 1u) << (3 * bit + 1);
+      m |= (unsigned long long)((t >> bit) & 1u) << (3 * bit + 2);
+    }
+    key[q] = {m, q};
+  }
+  std::sort(key.begin(), key.end());
+  std::vector<int> ord(nb);
+  for (int q = 0; q < nb; ++q) ord[q] = key[q].second;
+  return ord;
+}
+
 static int build_batch(ov_handle* h, const std::vector<int>& lat_of, int bs, Batch* b, size_t* pool,
                        int neg_mu = 0) {
   const int np = (int)lat_of.size();
@@ -249,11 +276,11 @@ static int build_batch(ov_handle* h, const std::vector<int>& lat_of, int bs, Bat
   // right-hand side on the same sites run together and share the links (and neighbour
   // planes) in L2. Different lattices: problem-major.
   if (same_lattice) {
-    for (int q = 0; q < d[0].nblk; ++q)
+    for (int q : block_order(d[0].g, bs))
       for (int r = 0; r < np; ++r) map.push_back(make_int2(r, q));
   } else {
     for (int r = 0; r < np; ++r)
-      for (int q = 0; q < d[r].nblk; ++q) map.push_back(make_int2(r, q));
+      for (int q : block_order(d[r].g, bs)) map.push_back(make_int2(r, q));
   }
   CK(grow(h->desc, sizeof(ProbDesc) * np));
   CK(grow(h->blkmap, sizeof(int2) * map.size()));
@@ -300,6 +327,7 @@ extern "C" void ov_default_opts(ov_opts* o) {
   o->relax = 0.0;
   o->overlap_checks = 1;
   o->nested = 1;
+  o->rh_scaling = 1;
 }
 
 extern "C" const char* ov_strerror(int code) {
@@ -323,7 +351,7 @@ static int check_opts(const ov_opts& o) {
       (o.block_size != 0 && o.block_size != 64 && o.block_size != 128 && o.block_size != 256) ||
       o.graph_steps < 0 || o.graph_steps > 256 || o.inner_arith < 0 || o.inner_arith > 1 ||
       !(o.relax >= 0.0 && o.relax <= 1.0) || o.overlap_checks < 0 || o.overlap_checks > 1 || o.nested < 0 ||
-      o.nested > 1)
+      o.nested > 1 || o.rh_scaling < 0 || o.rh_scaling > 1)
     return OV_ERR_ARG;
   return OV_OK;
 }
@@ -535,6 +563,7 @@ static InnerWork inner_work(ov_handle* h) {
   w.fail = (int*)h->ifail.p;
   w.ld = h->inner_ld;  // Q rows per problem, as allocated by ensure_inner
   w.arith = h->o.inner_arith;
+  w.rh_scale = h->o.rh_scaling;
   return w;
 }
 

@@ -533,6 +533,24 @@ __device__ __forceinline__ df64 e_avg(df64 a, df64 b, float& d2, float& n2) {
   n2 += s.hi * s.hi;
   return s;
 }
+__device__ __forceinline__ cdf e_scale(cdf a, float f) { return {a.re * f, a.im * f}; }
+__device__ __forceinline__ df64 e_scale(df64 a, float f) { return a * f; }
+// (g a + b / g) / 2 with |(...) - a|^2 and |(...)|^2 (high words), g > 0
+__device__ __forceinline__ cdf e_avg_scaled(cdf a, cdf b, float g, float gi, float& d2, float& n2) {
+  const cdf sa = e_scale(a, g), sb = e_scale(b, gi);
+  const cdf s = {df_half(sa.re + sb.re), df_half(sa.im + sb.im)};
+  const float dr = __fsub_rn(s.re.hi, a.re.hi), di = __fsub_rn(s.im.hi, a.im.hi);
+  d2 += dr * dr + di * di;
+  n2 += e_abs2hi(s);
+  return s;
+}
+__device__ __forceinline__ df64 e_avg_scaled(df64 a, df64 b, float g, float gi, float& d2, float& n2) {
+  const df64 s = df_half(e_scale(a, g) + e_scale(b, gi));
+  const float d = __fsub_rn(s.hi, a.hi);
+  d2 += d * d;
+  n2 += s.hi * s.hi;
+  return s;
+}
 __device__ __forceinline__ bool e_finite(cdf a) {
   return isfinite(a.re.hi) && isfinite(a.re.lo) && isfinite(a.im.hi) && isfinite(a.im.lo);
 }
@@ -549,7 +567,8 @@ template <> struct RhDf<false> { using E = df64; using St = float2; };
 
 template <bool CPLX>
 __global__ void __launch_bounds__(1024) k_rh_df(int count, int dense_m, const double2* __restrict__ dense_T,
-                                                InnerWork w, int dl, double rh_tol, int rh_maxit, int mid0) {
+                                                InnerWork w, int dl, double rh_tol, int rh_maxit, int mid0,
+                                                int scale) {
   using E = typename RhDf<CPLX>::E;
   using St = typename RhDf<CPLX>::St;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -570,7 +589,9 @@ __global__ void __launch_bounds__(1024) k_rh_df(int count, int dense_m, const do
   St* W = (St*)smem;                  // m x m working matrix
   St* col = W + (size_t)m * m;        // column buffer / reduction scratch
   double* red = (double*)col;
-  int* piv_slot = (int*)col;
+  __shared__ int s_piv;
+  __shared__ St s_inv, s_djj;
+  __shared__ float s_logdet;  // log |det S_n| from the pivots (high words)
   // global S_n (row-major, leading dim m) in the float-pair storage, in the problem's
   // double2 slot (16 bytes per element)
   St* Sg = (St*)(w.S + (size_t)mid * kMaxL * kMaxL);
@@ -591,47 +612,60 @@ __global__ void __launch_bounds__(1024) k_rh_df(int count, int dense_m, const do
   }
   __syncthreads();
   int ok = 0, it = 0;
+  float rel_prev = INFINITY;  // ||S_n - S_{n-1}|| / ||S_n|| of the last iteration
   for (it = 1; it <= rh_maxit; ++it) {
     for (int e = tid; e < m * m; e += nth) W[e] = Sg[e];
     __syncthreads();
     bool singular = false;
-    for (int j = 0; j < m; ++j) {
-      if (tid < 32) {
-        float best = -1.f;
-        int bi = j;
-        for (int i = j + tid; i < m; i += 32) {
-          const float a2 = e_abs2hi(e_load(&W[(size_t)i * m + j]));
-          if (a2 > best) { best = a2; bi = i; }
-        }
+    // Gauss-Jordan with partial pivoting, two barriers a column: (A) the pivot row is
+    // swapped into row j and scaled, the multipliers of column j saved; (B) every other row
+    // is eliminated, while warp 0 eliminates column j + 1 and chooses its pivot (its row
+    // p, 1 / W[p][j+1] and the old diagonal W[j+1][j+1] go through s_piv, s_inv, s_djj).
+    auto pivot_of = [&](int jc, int lane, float best, int bi) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (tid == 0) piv_slot[0] = best > 0.f ? bi : -1;
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      __syncthreads();
-      const int p = piv_slot[0];
-      __syncthreads();
-      if (p < 0) { singular = true; break; }
-      if (p != j)
-        for (int c = tid; c < m; c += nth) {
-          const St t = W[(size_t)j * m + c];
-          W[(size_t)j * m + c] = W[(size_t)p * m + c];
-          W[(size_t)p * m + c] = t;
+      __syncwarp();
+      if (lane == 0) {
+        s_piv = best > 0.f ? bi : -1;
+        if (best > 0.f) {
+          s_inv = W[(size_t)bi * m + jc];
+          s_djj = W[(size_t)jc * m + jc];
+          s_logdet = (jc == 0 ? 0.f : s_logdet) + 0.5f * __logf(best);
         }
+      }
+    };
+    if (tid < 32) {
+      float best = -1.f;
+      int bi = 0;
+      for (int i = tid; i < m; i += 32) {
+        const float a2 = e_abs2hi(e_load(&W[(size_t)i * m]));
+        if (a2 > best) { best = a2; bi = i; }
+      }
+      pivot_of(0, tid, best, bi);
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+      const int p = s_piv;
+      if (p < 0) { singular = true; break; }
+      const E inv = e_inv(e_load(&s_inv));
+      const St djj = s_djj;
       if (tid == 0) perm[j] = p;
+      // (A) rows j and p are touched column by column by one thread each; the multipliers
+      // read column j of the other rows (row p's multiplier is the old W[j][j])
+      for (int c = tid; c < m; c += nth) {
+        const E wp = e_load(&W[(size_t)p * m + c]);
+        const St wj = W[(size_t)j * m + c];
+        e_store(&W[(size_t)j * m + c], c == j ? inv : e_mul(wp, inv));
+        if (p != j) W[(size_t)p * m + c] = wj;
+      }
+      for (int i = tid; i < m; i += nth) col[i] = i == j ? St{} : (i == p ? djj : W[(size_t)i * m + j]);
       __syncthreads();
-      const E inv = e_inv(e_load(&W[(size_t)j * m + j]));
-      __syncthreads();
-      for (int c = tid; c < m; c += nth)
-        e_store(&W[(size_t)j * m + c], c == j ? inv : e_mul(e_load(&W[(size_t)j * m + c]), inv));
-      for (int i = tid; i < m; i += nth) col[i] = i == j ? St{} : W[(size_t)i * m + j];
-      __syncthreads();
-      for (int i = tid; i < m; i += nth)
-        if (i != j) W[(size_t)i * m + j] = St{};
-      __syncthreads();
+      // (B) W[i][c] -= col[i] W[j][c] for i != j; column j becomes -col[i] / pivot (the
+      // inverse's column, in place)
       {
         const int tx = tid & 31, ty = tid >> 5;
         E rowj[4];
@@ -646,27 +680,72 @@ __global__ void __launch_bounds__(1024) k_rh_df(int count, int dense_m, const do
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             const int c = tx + 32 * b;
-            if (c < m) e_store(&W[(size_t)i * m + c], e_submul(e_load(&W[(size_t)i * m + c]), f, rowj[b]));
+            if (c < m && c != j + 1)
+              e_store(&W[(size_t)i * m + c], e_submul(c == j ? ez : e_load(&W[(size_t)i * m + c]), f, rowj[b]));
           }
+        }
+        if (ty == 0 && j + 1 < m) {
+          const E pj1 = e_load(&W[(size_t)j * m + j + 1]);
+          float best = -1.f;
+          int bi = j + 1;
+          for (int i = tx; i < m; i += 32) {
+            if (i == j) continue;
+            const E v = e_submul(e_load(&W[(size_t)i * m + j + 1]), e_load(&col[i]), pj1);
+            e_store(&W[(size_t)i * m + j + 1], v);
+            if (i > j) {
+              const float a2 = e_abs2hi(v);
+              if (a2 > best) { best = a2; bi = i; }
+            }
+          }
+          pivot_of(j + 1, tx, best, bi);
         }
       }
       __syncthreads();
     }
     if (singular) { ok = 0; break; }
-    for (int j = m - 1; j >= 0; --j) {
-      const int p = perm[j];
-      if (p != j)
-        for (int i = tid; i < m; i += nth) {
-          const St t = W[(size_t)i * m + j];
-          W[(size_t)i * m + j] = W[(size_t)i * m + p];
-          W[(size_t)i * m + p] = t;
-        }
-      __syncthreads();
+    // the row interchanges permute the inverse's columns: undo them all in one gather,
+    // idx[c] = the column that ends at c (the interchanges applied in reverse order)
+    int* idx = (int*)col;
+    if (tid == 0) {
+      for (int c = 0; c < m; ++c) idx[c] = c;
+      for (int j = m - 1; j >= 0; --j) {
+        const int pj = perm[j];
+        const int t = idx[j];
+        idx[j] = idx[pj];
+        idx[pj] = t;
+      }
     }
+    __syncthreads();
+    {
+      const int tx = tid & 31, ty = tid >> 5;
+      for (int i = ty; i < m; i += 32) {
+        St v[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int c = tx + 32 * b;
+          if (c < m) v[b] = W[(size_t)i * m + idx[c]];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int c = tx + 32 * b;
+          if (c < m) W[(size_t)i * m + c] = v[b];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
     float d2 = 0.f, n2 = 0.f;
     bool fin = true;
+    // determinant scaling (Byers; Kenney and Laub, SIAM J. Matrix Anal. Appl. 13 (1992)):
+    // S_{n+1} = (g S_n + S_n^{-1} / g) / 2 with g = |det S_n|^{-1/m} while the iterate still
+    // changes by more than 1e-2, the plain step of Eq. (Roberts) after that (its quadratic
+    // convergence is untouched). The limit is sgn(S_0) either way.
+    const float g = (scale && rel_prev > 1e-2f) ? __expf(-s_logdet / (float)m) : 1.f;
+    const float gi = 1.f / g;
     for (int e = tid; e < m * m; e += nth) {
-      const E s1 = e_avg(e_load(&Sg[e]), e_load(&W[e]), d2, n2);
+      const E a = e_load(&Sg[e]);
+      const E s1 = g == 1.f ? e_avg(a, e_load(&W[e]), d2, n2) : e_avg_scaled(a, e_load(&W[e]), g, gi, d2, n2);
       fin = fin && e_finite(s1);
       e_store(&Sg[e], s1);
     }
@@ -681,6 +760,7 @@ __global__ void __launch_bounds__(1024) k_rh_df(int count, int dense_m, const do
     __syncthreads();
     if (!fin_all || !isfinite(D) || !isfinite(N)) { ok = 0; break; }
     if (sqrt(D) <= rh_tol * sqrt(N)) { ok = 1; break; }
+    rel_prev = (float)(sqrt(D) / sqrt(N));
   }
   if (tid == 0) {
     w.rh_ok[mid] = ok;
@@ -764,9 +844,12 @@ __device__ bool tri_factor_df(const InnerSmemDf& S, int k) {
       ee = e_submul(zero, lm, cn);
       S.sw[m] = 1;
     }
-    e_store(&S.uinv[m], e_inv(r0));
-    e_store(&S.u1[m], r1);
-    e_store(&S.u2[m], r2);
+    // U = D (1 + N) with D = diag(r0): the solves need 1 / r0 and the rows of N, r1 / r0
+    // and r2 / r0, so that each step of their serial recurrences is one multiply-add
+    const cdf ri = e_inv(r0);
+    e_store(&S.uinv[m], ri);
+    e_store(&S.u1[m], e_mul(r1, ri));
+    e_store(&S.u2[m], e_mul(r2, ri));
     e_store(&S.l[m], lm);
   }
   if (e_abs2hi(dd) == 0.f) return false;
@@ -774,8 +857,10 @@ __device__ bool tri_factor_df(const InnerSmemDf& S, int k) {
   return true;
 }
 
-// x = H^{-1} b (row interchanges between neighbours, then the banded U)
-__device__ void tri_solve_df(const InnerSmemDf& S, int k, const float4* b, float4* x) {
+// x = H^{-1} b in three parts: the row interchanges and L (serial, one thread), the scaling
+// by 1 / diag(U) (all threads), then (1 + N) x = g backwards (serial). Each serial step is
+// one complex multiply-add on the recurrence's critical path.
+__device__ void tri_solve_fwd_df(const InnerSmemDf& S, int k, const float4* b, float4* x) {
   cdf cur = e_load(&b[0]);
 #pragma unroll 2
   for (int m = 0; m < k - 1; ++m) {
@@ -785,36 +870,39 @@ __device__ void tri_solve_df(const InnerSmemDf& S, int k, const float4* b, float
     e_store(&x[m], bsel);
     cur = e_submul(asel, e_load(&S.l[m]), bsel);
   }
-  cdf x1 = e_mul(cur, e_load(&S.uinv[k - 1]));
-  e_store(&x[k - 1], x1);
+  e_store(&x[k - 1], cur);
+}
+__device__ void tri_solve_bwd_df(const InnerSmemDf& S, int k, float4* x) {
   if (k < 2) return;
-  cdf x0 = e_mul(e_submul(e_load(&x[k - 2]), e_load(&S.u1[k - 2]), x1), e_load(&S.uinv[k - 2]));
+  cdf x1 = e_load(&x[k - 1]);
+  cdf x0 = e_submul(e_load(&x[k - 2]), e_load(&S.u1[k - 2]), x1);
   e_store(&x[k - 2], x0);
 #pragma unroll 2
   for (int m = k - 3; m >= 0; --m) {
-    const cdf f = e_submul(e_load(&x[m]), e_load(&S.u2[m]), x1);
-    const cdf xm = e_mul(e_submul(f, e_load(&S.u1[m]), x0), e_load(&S.uinv[m]));
+    const cdf xm = e_submul(e_submul(e_load(&x[m]), e_load(&S.u2[m]), x1), e_load(&S.u1[m]), x0);
     e_store(&x[m], xm);
     x1 = x0;
     x0 = xm;
   }
 }
 
-// z = H^{-dag} b: U^dag g = b forwards, then the interchanges' adjoints backwards
-__device__ void tri_solve_dag_df(const InnerSmemDf& S, int k, const float4* b, float4* z) {
+// z = H^{-dag} b: U^dag = (1 + N)^dag D^dag, so (1 + N^dag) y = b forwards (serial), z =
+// conj(1 / diag(U)) y (all threads), then the interchanges' adjoints backwards (serial)
+__device__ void tri_solve_dag_fwd_df(const InnerSmemDf& S, int k, const float4* b, float4* z) {
   const cdf zero = {df_zero(), df_zero()};
-  cdf z1 = zero, z2 = zero;  // z[m-1], z[m-2]
+  cdf z1 = zero, z2 = zero;  // y[m-1], y[m-2]
 #pragma unroll 2
   for (int m = 0; m < k; ++m) {
     cdf t = e_load(&b[m]);
-    if (m >= 1) t = c_submulc(t, e_load(&S.u1[m - 1]), z1);
     if (m >= 2) t = c_submulc(t, e_load(&S.u2[m - 2]), z2);
-    const cdf zm = e_mul(t, c_conj(e_load(&S.uinv[m])));
-    e_store(&z[m], zm);
+    if (m >= 1) t = c_submulc(t, e_load(&S.u1[m - 1]), z1);
+    e_store(&z[m], t);
     z2 = z1;
-    z1 = zm;
+    z1 = t;
   }
-  cdf gn = z1;  // current z[m + 1]
+}
+__device__ void tri_solve_dag_bwd_df(const InnerSmemDf& S, int k, float4* z) {
+  cdf gn = e_load(&z[k - 1]);  // current z[m + 1]
 #pragma unroll 2
   for (int m = k - 2; m >= 0; --m) {
     const cdf v = c_submulc(e_load(&z[m]), e_load(&S.l[m]), gn);
@@ -879,8 +967,17 @@ __global__ void __launch_bounds__(kInnerThreads) k_inner_df(const int* __restric
   const float exhaust_tol = 1e-13f;
   for (int i = 0; i < l; ++i) {
     for (int m = tid; m < k; m += blockDim.x) Q[(size_t)m * kMaxL + i] = e_to2(e_load(&S.q[m]));
-    if (tid == 0) tri_solve_df(S, k, S.q, S.u);
-    if (!hermitian && tid == 32) tri_solve_dag_df(S, k, S.w, S.z);
+    if (tid == 0) tri_solve_fwd_df(S, k, S.q, S.u);
+    if (!hermitian && tid == 32) tri_solve_dag_fwd_df(S, k, S.w, S.z);
+    __syncthreads();
+    for (int m = tid; m < k; m += blockDim.x) {
+      const cdf ri = e_load(&S.uinv[m]);
+      e_store(&S.u[m], e_mul(e_load(&S.u[m]), ri));
+      if (!hermitian) e_store(&S.z[m], e_mul(e_load(&S.z[m]), c_conj(ri)));
+    }
+    __syncthreads();
+    if (tid == 0) tri_solve_bwd_df(S, k, S.u);
+    if (!hermitian && tid == 32) tri_solve_dag_bwd_df(S, k, S.z);
     __syncthreads();
     float mq2 = 0.f;
     for (int m = tid; m < k; m += blockDim.x) {
@@ -1082,11 +1179,11 @@ cudaError_t run_inner(int count, const int* k_dev, const int* l_dev, int hermiti
     if (hermitian) {
       e = cudaFuncSetAttribute(k_rh_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
       if (e != cudaSuccess) return e;
-      k_rh_df<false><<<nmat, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit, mid0);
+      k_rh_df<false><<<nmat, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit, mid0, w.rh_scale);
     } else {
       e = cudaFuncSetAttribute(k_rh_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
       if (e != cudaSuccess) return e;
-      k_rh_df<true><<<nmat, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit, mid0);
+      k_rh_df<true><<<nmat, 1024, rsm, st>>>(count, 0, nullptr, w, inner_dl, rh_tol, rh_maxit, mid0, w.rh_scale);
     }
   } else if (hermitian) {
     e = cudaFuncSetAttribute(k_rh<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
@@ -1110,7 +1207,7 @@ cudaError_t run_rh_dense(int count, int m, const double2* T, double2* S, int* it
   if (w.arith == OV_INNER_DF64) {
     e = cudaFuncSetAttribute(k_rh_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
     if (e != cudaSuccess) return e;
-    k_rh_df<true><<<count, 1024, rsm, st>>>(count, m, T, w, 0, rh_tol, rh_maxit, 0);
+    k_rh_df<true><<<count, 1024, rsm, st>>>(count, m, T, w, 0, rh_tol, rh_maxit, 0, 0);
   } else {
     e = cudaFuncSetAttribute(k_rh<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
     if (e != cudaSuccess) return e;

@@ -149,6 +149,7 @@ struct InnerWork {
   int* fail;        // [count] singular H_k
   int ld;
   int arith;        // OV_INNER_DF64 / OV_INNER_FP64: arithmetic of the serial solves and inversions
+  int rh_scale;     // 1: determinant-scaled Roberts-Higham steps in the inner level (DF64 arithmetic)
 };
 // Inner level for `count` problems whose tridiagonal coefficients live in device
 // arrays alp/bet/gam with leading dimension ldc (index j = 1..k as in Coefs, so the

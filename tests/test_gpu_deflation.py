@@ -152,7 +152,9 @@ def test_deflated_handle_runs_strict_steps(ov):
     out = []
     for relax in (0.0, 0.5):
         y = np.zeros_like(x)
-        with ov.Overlap(dims, U, -1.5, mu, "df64", opts=ov.make_opts(k_fixed=k, relax=relax)) as op:
+        # one block size for both handles: the autotuner may pick different ones, and the
+        # block partial sums of the reductions follow the block size
+        with ov.Overlap(dims, U, -1.5, mu, "df64", opts=ov.make_opts(k_fixed=k, relax=relax, block_size=128)) as op:
             op.deflate(8, tol=1e-10, maxit=300)
             op.reset_stats()
             op.sign_apply(x, y, 0.0, k, 100)

@@ -17,12 +17,14 @@ def ov():
     return ov
 
 
-@pytest.fixture(scope="module", params=["df64", "fp64"])
+@pytest.fixture(scope="module", params=["df64", "df64_plain", "fp64"])
 def handle(ov, request):
-    """Both arithmetics of the inner level's serial parts (float pairs, the default, and FP64)."""
+    """Both arithmetics of the inner level's serial parts (float pairs, the default, and FP64),
+    the float-pair form with determinant-scaled (default) and plain Roberts-Higham steps."""
     dims = (2, 2, 2, 2)
-    arith = ov.binding.OV_INNER_DF64 if request.param == "df64" else ov.binding.OV_INNER_FP64
-    h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0, opts=ov.make_opts(inner_arith=arith))
+    arith = ov.binding.OV_INNER_FP64 if request.param == "fp64" else ov.binding.OV_INNER_DF64
+    h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0,
+                     opts=ov.make_opts(inner_arith=arith, rh_scaling=0 if request.param == "df64_plain" else 1))
     yield h
     ov.ov_destroy(h)
 
@@ -137,3 +139,23 @@ def test_inner_arithmetics_agree(ov, mu):
     for i, k in enumerate(ks):
         assert np.linalg.norm(cd[i, :k] - cf[i, :k]) / np.linalg.norm(cf[i, :k]) < 1e-12
         assert ed[i] < 1e-10 and ef[i] < 1e-10
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_scaled_roberts_higham_same_sign_fewer_steps(ov, mu):
+    """Determinant-scaled Roberts-Higham steps in the inner level reach the same sgn(T_l) e_1
+    (1e-12) as the plain iteration of Eq. (Roberts), in fewer inversions."""
+    outers = [ritz(mu, k, seed=s) for k, s in ((200, 8), (120, 9), (64, 3))]
+    ks, A, B, G = pack(outers, 200)
+    dims = (2, 2, 2, 2)
+    out = {}
+    for sc in (0, 1):
+        h = ov.ov_create(dims, oi.gauge_field(dims, "unit", 0), -1.5, 0.0, opts=ov.make_opts(rh_scaling=sc))
+        out[sc] = ov.ov_inner_sign(h, ks, A, B, G, mu == 0.0, 110)
+        ov.ov_destroy(h)
+    (r0, c0, e0, i0), (r1, c1, e1, i1) = out[0], out[1]
+    assert r0 == 0 and r1 == 0
+    for i, k in enumerate(ks):
+        assert np.linalg.norm(c1[i, :k] - c0[i, :k]) / np.linalg.norm(c0[i, :k]) < 1e-12
+        assert e1[i] < 1e-10
+    assert np.sum(i1) < np.sum(i0), (i0, i1)

@@ -92,7 +92,11 @@ def test_c2_two_sided_stopping_rule_8444(ov, prec):
     oracle's own stopping run (it stops at k = 310). The stop is a threshold decision on
     an estimate carrying roundoff, so the two may stop one check apart (the estimate at
     k = 300 sits at 1e-10 while the answer there is 3.8e-10 from the one at k = 310);
-    the GPU answer is then compared with the oracle run to the GPU's own k."""
+    the GPU answer is then compared with the oracle run to the GPU's own k. The two-sided
+    process at k = 310 amplifies differences of arithmetic: a 1e-15 relative change of x
+    moves the oracle's own k = 310 answer by 1e-11, so the double-float run (2^-48 a
+    rounding against FP64's 2^-53) agrees with the FP64 oracle to a few 1e-10 there (the
+    inner level at this k is not sensitive: a 1e-14 change of H_k moves c by 1e-13)."""
     dims = (8, 8, 8, 8)
     U = oi.gauge_field(dims, "near_unit", 0, eps=0.4)
     x = oi.gaussian_source(dims, 1)
@@ -102,7 +106,8 @@ def test_c2_two_sided_stopping_rule_8444(ov, prec):
     assert abs(info[0]["k"] - io["k"]) <= 10
     if info[0]["k"] != io["k"]:
         yo, io = oracle_sign(U, dims, -1.5, 0.3, x, k_max=800, l=100, tol=0, k_fixed=info[0]["k"])
-    assert rel(y[0], yo) < 1e-10, (info[0]["k"], io["k"], rel(y[0], yo))
+    bar = 1e-10 if prec == "fp64" else 3e-10
+    assert rel(y[0], yo) < bar, (info[0]["k"], io["k"], rel(y[0], yo))
 
 
 def test_free_field_closed_form(ov):
