@@ -723,7 +723,7 @@ def extra_configs(ov, torch):
     dims = [p["dims"] for p in probs]
     mws, mus = [p["m_w"] for p in probs], [p["mu"] for p in probs]
     res = {}
-    theta = sizer.load(sizer.DEFAULT_PARAMS)
+    theta_rough = sizer.load(sizer.ROUGH_PARAMS)
     defl, sched = {}, {}
     # the float, strict and deflated lines place their checks adaptively (check_schedule = 1):
     # a check of the 48 lattices costs ~20 ms, ~90 of the batch's outer steps, and the batch
@@ -738,7 +738,8 @@ def extra_configs(ov, torch):
         hb = ov.ov_batch_create(dims, Us, mws, mus, prec, opts=ov.make_opts(**ob))
         try:
             if form == "df64":
-                ov.ov_set_sizer(hb, theta, 8, L_MAX)
+                # half of the batch's lattices carry Haar links: the sizing trained with rough fields
+                ov.ov_set_sizer(hb, theta_rough, 8, L_MAX)
             if form == "df64_deflated":
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -769,7 +770,8 @@ def extra_configs(ov, torch):
             "graph_launches": st["graph_launches"], "block_size": st["block_size"],
             "checks": st["checks"], "check_schedule": sched[form],
             "form": {"fp32": "float vectors and links",
-                     "df64": "double-float, learned sizing, float hopping from %.1f x k* on" % RELAX,
+                     "df64": ("double-float, learned sizing (the parameters trained with rough fields), float "
+                              "hopping from %.1f x k* on" % RELAX),
                      "df64_strict": "double-float, strict steps, no sizing, no deflation",
                      "df64_deflated": ("double-float, strict steps, no sizing, the %d eigenpairs of smallest |lambda| "
                                        "per lattice deflated (Sec. 2; pairs with residual <= %g kept; setup not in ms)"

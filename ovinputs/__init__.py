@@ -24,5 +24,7 @@ from .gen import (  # noqa: F401
     round_links_fp32,
     problem_batch_48,
     training_problems,
+    training_problems_rough,
+    training_problems_large,
     problem_source,
 )

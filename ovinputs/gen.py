@@ -144,6 +144,48 @@ def training_problems(count=2000, seed_base=1000):
     return out
 
 
+def training_problems_rough(count=400, seed_base=20000):
+    """Problems for learning (k, l) that include rough fields and the shapes of the
+    48-lattice batch: 4^4, 6^4, 6^3x8, 6^3x12, 8^3x6, 8^4; Haar links (half of them) or
+    near-unit links with eps ~ U[0.2, 0.5]; mu ~ U[0, 0.5], m_w ~ U[-1.8, -1.3]; seeds
+    seed_base + i (disjoint from the batch's and from training_problems'); a Gaussian
+    source (even i) or a spin-colour point source at site 0 (odd i)."""
+    shapes = [(4, 4, 4, 4), (6, 6, 6, 6), (6, 6, 6, 8), (6, 6, 6, 12), (8, 8, 8, 6), (8, 8, 8, 8)]
+    out = []
+    for i in range(count):
+        rng = np.random.Generator(np.random.PCG64(seed_base + i))
+        dims = shapes[int(rng.integers(0, len(shapes)))]
+        kind = "haar" if rng.uniform() < 0.5 else "near_unit"
+        mu = float(rng.uniform(0.0, 0.5))
+        eps = float(rng.uniform(0.2, 0.5))
+        m_w = float(rng.uniform(-1.8, -1.3))
+        sc = int(rng.integers(0, 12))
+        out.append(dict(dims=dims, kind=kind, eps=eps if kind == "near_unit" else 0.0, mu=mu, m_w=m_w,
+                        gauge_seed=seed_base + i, source_seed=seed_base + i + 100000,
+                        source="gaussian" if i % 2 == 0 else "point", spin=sc // 3, colour=sc % 3))
+    return out
+
+
+def training_problems_large(count=120, seed_base=40000):
+    """Larger problems for learning (k, l): 10^4, 12^4, 12^3x16, 16^4, near-unit links with
+    eps ~ U[0.2, 0.5], mu ~ U[0, 0.5], m_w ~ U[-1.8, -1.3]; seeds seed_base + i (disjoint
+    from every evaluation workload's); a Gaussian source (even i) or a spin-colour point
+    source at site 0 (odd i)."""
+    shapes = [(10, 10, 10, 10), (12, 12, 12, 12), (12, 12, 12, 16), (16, 16, 16, 16)]
+    out = []
+    for i in range(count):
+        rng = np.random.Generator(np.random.PCG64(seed_base + i))
+        dims = shapes[int(rng.integers(0, len(shapes)))]
+        mu = float(rng.uniform(0.0, 0.5))
+        eps = float(rng.uniform(0.2, 0.5))
+        m_w = float(rng.uniform(-1.8, -1.3))
+        sc = int(rng.integers(0, 12))
+        out.append(dict(dims=dims, kind="near_unit", eps=eps, mu=mu, m_w=m_w,
+                        gauge_seed=seed_base + i, source_seed=seed_base + i + 100000,
+                        source="gaussian" if i % 2 == 0 else "point", spin=sc // 3, colour=sc % 3))
+    return out
+
+
 def problem_source(p):
     """The source of a problem dict from training_problems / problem_batch_48."""
     if p.get("source", "gaussian") == "point":

@@ -18,6 +18,13 @@ coefficients.
 
     python -m paper_0910_2918_gb300.sizer --records N --out data.npz   # generate
     python -m paper_0910_2918_gb300.sizer --train data.npz --out sizer.npz
+
+The two parameter sets in the package were made by (data/ holds the records)
+    --train data/sizer_records.npz --out sizer_params.npz
+    --records 2200 --k-max 1000; --records 300 --rough --k-max 1000;
+    --records 120 --large --k-max 1000 (the three record files), then
+    --train data/sizer_records_nu_k1000.npz --also data/sizer_records_rough.npz
+            data/sizer_records_large.npz --ablation --out sizer_params_rough.npz
 """
 import argparse
 import os
@@ -83,10 +90,31 @@ def convergence_record(dims, U, m_w, mu, x, tol=1e-8, k_max=600, dk=10, precisio
             np.concatenate([a[:16], b[1:17], g[1:17]]).astype(np.complex128))
 
 
-def features_from_raw(raw):
-    """Features from stored raw coefficients [alpha_1..16, beta_2..17, gamma_2..17]."""
+def features_from_raw(raw, fset="a6i6b4"):
+    """Features from stored raw coefficients [alpha_1..16, beta_2..17, gamma_2..17]:
+    a6i6b4 (the network's: Re alpha_1..6, Im alpha_1..6, beta_2..5), or for comparison
+    a8b8 (the first 16 outer coefficients: Re alpha_1..8, beta_2..9), a4i4b8
+    (Re alpha_1..4, Im alpha_1..4, beta_2..9), a8i8 (Re and Im alpha_1..8)."""
     raw = np.asarray(raw)
-    return np.concatenate([np.real(raw[:, :6]), np.imag(raw[:, :6]), np.real(raw[:, 16:20])], axis=1)
+    a, b = raw[:, :16], raw[:, 16:32]
+    parts = {"a6i6b4": [np.real(a[:, :6]), np.imag(a[:, :6]), np.real(b[:, :4])],
+             "a8b8": [np.real(a[:, :8]), np.real(b[:, :8])],
+             "a4i4b8": [np.real(a[:, :4]), np.imag(a[:, :4]), np.real(b[:, :8])],
+             "a8i8": [np.real(a[:, :8]), np.imag(a[:, :8])]}[fset]
+    return np.concatenate(parts, axis=1)
+
+
+FEATURE_SETS = ["a6i6b4", "a8b8", "a4i4b8", "a8i8"]
+
+
+def held_out_errors(theta, F, k, l):
+    """Median and 90th percentile of |k_pred / k* - 1| and of |l_pred - l*|."""
+    kp, lp = predict(theta, F)
+    ek = np.abs(kp / k - 1.0)
+    el = np.abs(lp - l)
+    return {"k_rel_median": float(np.median(ek)), "k_rel_p90": float(np.percentile(ek, 90)),
+            "l_abs_median": float(np.median(el)), "l_abs_p90": float(np.percentile(el, 90)),
+            "k_under_20pct": float(np.mean(kp < 0.8 * k))}
 
 
 def make_dataset(problems, tol=1e-8, k_max=600, log_every=50):
@@ -167,7 +195,14 @@ def load(path):
     return d["theta"]
 
 
-DEFAULT_PARAMS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "sizer_params.npz")
+_HERE = os.path.dirname(os.path.abspath(__file__))
+# trained on the near-unit records (6^4 to 8^4, k <= 600): the parameters of the smooth
+# fields of the 16^4 and 24^3 x 48 workloads
+DEFAULT_PARAMS = os.path.join(_HERE, "sizer_params.npz")
+# trained on near-unit records with k <= 1000, rough (Haar) and near-unit records of the
+# 48-lattice batch's shapes, and near-unit records from 10^4 to 16^4: for ensembles with
+# rough fields
+ROUGH_PARAMS = os.path.join(_HERE, "sizer_params_rough.npz")
 
 
 def main():
@@ -178,23 +213,48 @@ def main():
     ap.add_argument("--out", required=True)
     ap.add_argument("--epochs", type=int, default=600)
     ap.add_argument("--train-n", type=int, default=2000, help="use the first N records (the rest stay held out)")
+    ap.add_argument("--rough", action="store_true",
+                    help="records from training_problems_rough (Haar and near-unit links, the batch's shapes)")
+    ap.add_argument("--large", action="store_true", help="records from training_problems_large (10^4 to 16^4)")
+    ap.add_argument("--k-max", type=int, default=600, help="outer dimension of a record's run")
+    ap.add_argument("--also", nargs="*", default=[],
+                    help="more record files: their first 85%% join the training set, the rest the held-out set")
+    ap.add_argument("--ablation", action="store_true", help="train every feature set, report held-out errors")
     args = ap.parse_args()
     if args.records:
         import ovinputs as oi
 
-        probs = oi.training_problems(args.first + args.records)[args.first:]
-        d = make_dataset(probs)
+        gen = (oi.training_problems_rough if args.rough else
+               oi.training_problems_large if args.large else oi.training_problems)
+        probs = gen(args.first + args.records)[args.first:]
+        d = make_dataset(probs, k_max=args.k_max)
         np.savez(args.out, **d)
         print(f"wrote {args.out}: converged {int(d['conv'].sum())}/{len(probs)}")
     if args.train:
-        d = np.load(args.train)
+        sets = [np.load(args.train)] + [np.load(f) for f in args.also]
         n = args.train_n
-        m = d["conv"][:n].astype(bool)
-        F = (features_from_raw(d["raw"]) if "raw" in d else d["F"])[:n]
-        theta, hist, vhist = train(F[m], d["k"][:n][m], d["l"][:n][m], epochs=args.epochs)
-        save(args.out, theta, loss=hist, val_loss=vhist, n_train=int(m.sum()))
-        print(f"wrote {args.out}: best validation loss {vhist.min():.4f} (epoch {int(vhist.argmin())}) "
-              f"on {int(m.sum())} records")
+        parts_tr, parts_ho = [], []
+        for i, d in enumerate(sets):
+            cut = n if i == 0 else int(0.85 * len(d["k"]))
+            m = d["conv"].astype(bool)
+            idx = np.arange(len(m))
+            parts_tr.append((d, idx[(idx < cut) & m]))
+            parts_ho.append((d, idx[(idx >= cut) & m]))
+
+        def gather(parts, fset):
+            F = np.concatenate([features_from_raw(d["raw"], fset)[ix] for d, ix in parts])
+            return F, np.concatenate([d["k"][ix] for d, ix in parts]), np.concatenate([d["l"][ix] for d, ix in parts])
+
+        for fset in (FEATURE_SETS if args.ablation else ["a6i6b4"]):
+            F, k, l = gather(parts_tr, fset)
+            theta, hist, vhist = train(F, k, l, epochs=args.epochs)
+            Fh, kh, lh = gather(parts_ho, fset)
+            err = held_out_errors(theta, Fh, kh, lh) if len(kh) else {}
+            print(f"features {fset}: {len(k)} training records, best validation loss {vhist.min():.4f} "
+                  f"(epoch {int(vhist.argmin())}); held out ({len(kh)} records): {err}", flush=True)
+            if fset == "a6i6b4":
+                save(args.out, theta, loss=hist, val_loss=vhist, n_train=len(k))
+                print(f"wrote {args.out}")
 
 
 if __name__ == "__main__":

@@ -57,3 +57,44 @@ def test_committed_network_on_held_out_records():
     el = np.abs(y[:, 1] - np.log(d["l"][m]))
     assert np.median(ek) < 0.25 and np.quantile(ek, 0.9) < 0.6
     assert np.median(el) < 0.25
+
+
+def test_rough_network_on_its_held_out_records():
+    """The parameters trained with rough fields, on the held-out part of the records they
+    were trained beside (the last 15% of the rough and large sets, records 2000 on of the
+    near-unit set at k <= 1000): k* within a median |log(k_pred / k*)| of 0.25, also on
+    the Haar lattices, where the near-unit parameters were never trained."""
+    import os
+
+    from paper_0910_2918_gb300 import sizer
+
+    theta = sizer.load(sizer.ROUGH_PARAMS)
+    assert theta.dtype == np.float32 and theta.size == mlp.N_PARAMS and np.all(np.isfinite(theta))
+    base = os.path.join(os.path.dirname(sizer.__file__), "data")
+    for name, cut in (("sizer_records_nu_k1000.npz", 2000), ("sizer_records_rough.npz", None),
+                      ("sizer_records_large.npz", None)):
+        d = np.load(os.path.join(base, name))
+        n = len(d["k"])
+        held = np.arange(n) >= (cut if cut is not None else int(0.85 * n))
+        m = held & d["conv"].astype(bool)
+        assert m.sum() >= 10
+        y, _ = mlp.forward(theta.astype(np.float64), sizer.features_from_raw(d["raw"])[m])
+        ek = np.abs(y[:, 0] - np.log(d["k"][m]))
+        assert np.median(ek) < 0.25, (name, np.median(ek))
+
+
+def test_feature_sets_of_the_ablation():
+    """Each feature set of the comparison has 16 entries (the network's input), drawn from
+    the first 16 outer coefficients as named."""
+    from paper_0910_2918_gb300 import sizer
+
+    rng = np.random.default_rng(5)
+    alpha = rng.standard_normal(16) + 1j * rng.standard_normal(16)
+    beta = np.concatenate([[0.0], rng.uniform(0.1, 1.0, 16)]).astype(complex)
+    raw = np.concatenate([alpha, beta[1:17], np.zeros(16)])[None, :]
+    for fs in sizer.FEATURE_SETS:
+        assert sizer.features_from_raw(raw, fs).shape == (1, 16)
+    f = sizer.features_from_raw(raw, "a8b8")[0]
+    assert np.array_equal(f[:8], alpha[:8].real) and np.array_equal(f[8:], beta[1:9].real)
+    f = sizer.features_from_raw(raw, "a4i4b8")[0]
+    assert np.array_equal(f[4:8], alpha[:4].imag) and np.array_equal(f[8:], beta[1:9].real)
