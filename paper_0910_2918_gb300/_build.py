@@ -16,6 +16,9 @@ SOURCES = ["ov_outer.cu", "ov_inner.cu", "ov_api.cu", "ov_noalloc.cu", "ov_mlp.c
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]
+# OV_NVCC_FLAGS: extra nvcc flags, e.g. "-DOV_STEP_THREADS_F32=768" to build another register
+# split of the step kernels (csrc/ov_outer.cu lists the build-time parameters)
+FLAGS += os.environ.get("OV_NVCC_FLAGS", "").split()
 
 
 def nvcc():
