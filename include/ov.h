@@ -131,7 +131,7 @@ typedef struct {
                            components along the removed eigenvectors, and measured on the
                            48-lattice batch 13 of 48 lattices then stop converging [0] */
   int overlap_checks;   /* 1: a stopping check runs on a second, high-priority stream while up to
-                           20 further outer steps (fewer than check_interval) run speculatively;
+                           24 further outer steps (fewer than check_interval) run speculatively;
                            a run that stops at the check uses k = the check's step, so results
                            are those of the serial order (not used where the previous check's
                            largest outer estimate was within 8 tol, where a stop is likely);

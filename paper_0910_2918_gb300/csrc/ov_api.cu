@@ -48,7 +48,7 @@ namespace {
 
 constexpr int kChunk = 64;       // outer basis slots per allocation chunk
 constexpr int kSizerSteps = 16;  // outer steps whose coefficients feed the learned sizing
-constexpr int kSpecSteps = 20;   // speculative outer steps run while a check is evaluated
+constexpr int kSpecSteps = 24;   // speculative outer steps run while a check is evaluated
 constexpr double kSpecFactor = 8.0;  // no speculation when the last estimate was within this of tol
 
 struct Buf {
@@ -1052,8 +1052,8 @@ static int sign_apply_core(ov_handle* h, int nrhs, const void* x, void* y, int m
     }
     if (h->trace) {
       const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc0).count();
-      fprintf(stderr, "{\"ov_check\": %d, \"ms\": %.3f, \"inner_estimate\": %d, \"rh_iters\": [", j, ms,
-              want_inner ? 1 : 0);
+      fprintf(stderr, "{\"ov_check\": %d, \"ms\": %.3f, \"speculative_steps\": %d, \"inner_estimate\": %d, \"rh_iters\": [",
+              j, ms, spec, want_inner ? 1 : 0);
       for (int r = 0; r < nrhs; ++r) fprintf(stderr, "%s%d", r ? "," : "", rhit[r]);
       fprintf(stderr, "], \"est_outer\": [");
       for (int r = 0; r < nrhs; ++r) fprintf(stderr, "%s%.3e", r ? "," : "", eo[r]);
