@@ -61,7 +61,7 @@ PROFILE_RELAXED = os.path.join(ROOT, "profiles", "stencil_twosided_relaxed_16x16
 GOLDEN = os.path.join(ROOT, "tests", "golden", "c3_16x16x16x16_mu0.2_sign.json")
 # mixed form of the headline: outer steps from RELAX x (learned k*) on run the hopping sum in
 # float (vectors, recurrence, reductions and coefficients stay double-float)
-RELAX = 0.4
+RELAX = 0.3
 
 
 def workload_desc():
