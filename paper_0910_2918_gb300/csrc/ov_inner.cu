@@ -613,6 +613,12 @@ __global__ void __launch_bounds__(1024) k_rh_df(int count, int dense_m, const do
   __syncthreads();
   int ok = 0, it = 0;
   float rel_prev = INFINITY;  // ||S_n - S_{n-1}|| / ||S_n|| of the last iteration
+  // the elimination's element share of thread tid >= 32 (warps 1..): the elements
+  // u, u + nth - 32, ... of the (m - 1) x (m - 1) block, row-major (u = tid - 32)
+  const int mm = m - 1;
+  const int fu = tid - 32, fst = nth - 32;
+  const int fr0 = (mm > 0 && fu >= 0) ? fu / mm : 0, fc0 = (mm > 0 && fu >= 0) ? fu % mm : 0;
+  const int fdr = mm > 0 ? fst / mm : 0, fdc = mm > 0 ? fst % mm : 0;
   for (it = 1; it <= rh_maxit; ++it) {
     for (int e = tid; e < m * m; e += nth) W[e] = Sg[e];
     __syncthreads();
@@ -665,39 +671,43 @@ __global__ void __launch_bounds__(1024) k_rh_df(int count, int dense_m, const do
       for (int i = tid; i < m; i += nth) col[i] = i == j ? St{} : (i == p ? djj : W[(size_t)i * m + j]);
       __syncthreads();
       // (B) W[i][c] -= col[i] W[j][c] for i != j; column j becomes -col[i] / pivot (the
-      // inverse's column, in place)
+      // inverse's column, in place). Warp 0 takes column cw = j + 1 (j itself at the last
+      // column) and, for j + 1 < m, picks that column's pivot; warps 1.. share the other
+      // (m - 1) x (m - 1) elements evenly (rows without j, columns without cw).
       {
-        const int tx = tid & 31, ty = tid >> 5;
-        E rowj[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int c = tx + 32 * b;
-          rowj[b] = c < m ? e_load(&W[(size_t)j * m + c]) : ez;
-        }
-        for (int i = ty; i < m; i += 32) {
-          if (i == j) continue;
-          const E f = e_load(&col[i]);
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int c = tx + 32 * b;
-            if (c < m && c != j + 1)
-              e_store(&W[(size_t)i * m + c], e_submul(c == j ? ez : e_load(&W[(size_t)i * m + c]), f, rowj[b]));
+        const int tx = tid & 31;
+        const int cw = j + 1 < m ? j + 1 : j;
+        if (tid >= 32) {
+          if (mm > 0) {
+            int ri = fr0, ci = fc0;
+            while (ri < mm) {
+              const int i = ri + (ri >= j);
+              const int c = ci + (ci >= cw);
+              const E f = e_load(&col[i]);
+              const E pj = e_load(&W[(size_t)j * m + c]);
+              e_store(&W[(size_t)i * m + c], e_submul(c == j ? ez : e_load(&W[(size_t)i * m + c]), f, pj));
+              ri += fdr;
+              ci += fdc;
+              if (ci >= mm) {
+                ci -= mm;
+                ++ri;
+              }
+            }
           }
-        }
-        if (ty == 0 && j + 1 < m) {
-          const E pj1 = e_load(&W[(size_t)j * m + j + 1]);
+        } else {
+          const E pj1 = e_load(&W[(size_t)j * m + cw]);
           float best = -1.f;
           int bi = j + 1;
           for (int i = tx; i < m; i += 32) {
             if (i == j) continue;
-            const E v = e_submul(e_load(&W[(size_t)i * m + j + 1]), e_load(&col[i]), pj1);
-            e_store(&W[(size_t)i * m + j + 1], v);
-            if (i > j) {
+            const E v = e_submul(cw == j ? ez : e_load(&W[(size_t)i * m + cw]), e_load(&col[i]), pj1);
+            e_store(&W[(size_t)i * m + cw], v);
+            if (cw == j + 1 && i > j) {
               const float a2 = e_abs2hi(v);
               if (a2 > best) { best = a2; bi = i; }
             }
           }
-          pivot_of(j + 1, tx, best, bi);
+          if (cw == j + 1) pivot_of(j + 1, tx, best, bi);
         }
       }
       __syncthreads();
