@@ -591,7 +591,9 @@ __device__ __forceinline__ cx<df64> smulsub(cx<df64> s, cx<df64> q, cx<df64> c, 
   if (RS) return {df_axpy2(q.re * s.re, -c.re, w.re, c.im, w.im), df_axpy2(q.im * s.re, -c.re, w.im, -c.im, w.re)};
   if (RC)
     return {df_axpy2(-(w.re * c.re), s.re, q.re, -s.im, q.im), df_axpy2(-(w.im * c.re), s.re, q.im, s.im, q.re)};
-  return smul<false>(s, q) - smul<false>(c, w);
+  // both complex: each component one compensated four-term sum
+  return {df_dot4(s.re, q.re, -s.im, q.im, -c.re, w.re, c.im, w.im),
+          df_dot4(s.re, q.im, s.im, q.re, -c.re, w.im, -c.im, w.re)};
 }
 // out = scl (gamma5 D t_j) - cf t_{j-1} at one site, 12 components, with t_j the
 // unnormalised current vector (psi) and t_{j-1} the previous one; the alpha partial: Lanczos

@@ -212,6 +212,23 @@ __device__ __forceinline__ df64 df_axpy2(df64 a, df64 x1, df64 y1, df64 x2, df64
   const float lo = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, s.lo), t.lo), __fadd_rn(e1, e2));
   return df_fast_two_sum(t.hi, lo);
 }
+// x1 y1 + x2 y2 + x3 y3 + x4 y4 in float pairs: every product exact as (p, e), the four
+// high words summed by TwoSum, every low word once, one renormalisation
+__device__ __forceinline__ df64 df_dot4(df64 x1, df64 y1, df64 x2, df64 y2, df64 x3, df64 y3, df64 x4, df64 y4) {
+  const float p1 = __fmul_rn(x1.hi, y1.hi), p2 = __fmul_rn(x2.hi, y2.hi);
+  const float p3 = __fmul_rn(x3.hi, y3.hi), p4 = __fmul_rn(x4.hi, y4.hi);
+  float e1 = __fmaf_rn(x1.hi, y1.hi, -p1), e2 = __fmaf_rn(x2.hi, y2.hi, -p2);
+  float e3 = __fmaf_rn(x3.hi, y3.hi, -p3), e4 = __fmaf_rn(x4.hi, y4.hi, -p4);
+  e1 = __fmaf_rn(x1.lo, y1.hi, __fmaf_rn(x1.hi, y1.lo, e1));
+  e2 = __fmaf_rn(x2.lo, y2.hi, __fmaf_rn(x2.hi, y2.lo, e2));
+  e3 = __fmaf_rn(x3.lo, y3.hi, __fmaf_rn(x3.hi, y3.lo, e3));
+  e4 = __fmaf_rn(x4.lo, y4.hi, __fmaf_rn(x4.hi, y4.lo, e4));
+  const df64 s = df_two_sum(p1, p2);
+  const df64 t = df_two_sum(s.hi, p3);
+  const df64 u = df_two_sum(t.hi, p4);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(s.lo, t.lo), u.lo), __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, e4)));
+  return df_fast_two_sum(u.hi, lo);
+}
 // a + x y
 __device__ __forceinline__ df64 df_axpy1(df64 a, df64 x, df64 y) {
   const float p = __fmul_rn(x.hi, y.hi);
