@@ -235,10 +235,13 @@ int ov_solve(ov_handle* h, int nrhs, const void* b, void* x, int mem, double mas
  * on the device for every lattice of the handle and attaches them: from then on every
  * apply of the handle (ov_sign_apply, ov_apply, ov_batch_sign_apply, ov_solve) deflates
  * (m = 0 detaches). Eigensolver: subspace iteration on a block of 2 m + 8 vectors (at most 64) with
- * a Chebyshev filter of degree 16 in A^2, Rayleigh-Ritz with A^2 on the block and with A on
- * its leading m vectors, until every residual
- * ||A r - lambda r|| <= tol ||A|| (maxit iterations at most); at mu != 0 a second run on
- * A^dag gives the left eigenvectors. m <= 48 (OV_ERR_TOO_LARGE), 2 m + 8 <= 12 V. Only the
+ * a Chebyshev filter in A^2 (degree up to 48, lower while the amplification would exceed 1e6),
+ * Rayleigh-Ritz with A^2 on the block and with A on its leading m vectors, until every
+ * residual ||A r - lambda r|| <= tol ||A|| (maxit iterations at most); at mu != 0 a second
+ * job on A^dag = gamma5 D_w(-mu) gives the left eigenvectors. All lattices of the handle
+ * (and both sides) iterate together: every matvec is one launch over all of them. The
+ * call synchronises the handle's stream and allocates its work space (several blocks of
+ * 2 m + 8 vectors of every lattice). m <= 48 (OV_ERR_TOO_LARGE), 2 m + 8 <= 12 V. Only the
  * pairs whose residual (right and left) is within tol are attached: the formula is exact
  * for any set of true eigenpairs, and a poor pair would put its error into the exact part;
  * the Krylov part then sees the spectrum with the attached ones removed. lam_out: 2 m
