@@ -18,11 +18,11 @@
 // through the QR factorisation of their coefficients, then Rayleigh-Ritz with A on the
 // leading m of them (the projected b x b and m x m problems are solved on the host,
 // ov_small.cpp), residuals ||A x - lambda x||. At mu != 0 the left eigenvectors are the right eigenvectors of
-// A^dag = gamma5 D_w(-mu) for conj(lambda): a second run with A^dag, matched by eigenvalue and
+// A^dag = gamma5 D_w(-mu) for conj(lambda): a second job on A(-mu), matched by eigenvalue and
 // biorthonormalised (L <- L (L^dag R)^{-dag}).
 //
 // All n-vectors are canonical complex doubles on the device; the matvecs run in the handle's
-// arithmetic (ov_api.cu: apply_block).
+// arithmetic (ov_api.cu: ApplySet, one launch over every job of an iteration).
 #include <math.h>
 #include <stdio.h>
 
